@@ -1,0 +1,293 @@
+"""Plain CPU oracle for fast fermion sampling (FFS), arXiv 2109.07358.
+
+THIS IS TEST INFRASTRUCTURE.  Only the test suite, the package smoke check and the
+CPU-baseline leg of the benchmark may import it.  The product path (the CUDA library
+and its Python binding) never calls it and shares no code with it.
+
+It is written for a reader checking it against the paper, not for speed: FP64 /
+complex128 NumPy, one sample at a time, the steps in the paper's order.
+
+Problem (Eq. 1): draw an ordered N-tuple x = (x_1..x_N), x_j in {0..L-1} (0-based
+here; the paper is 1-based), from P(x) = |det U_{x,n}|^2 / N!, U an L x N matrix with
+U^dagger U = 1.
+
+Method (main text around Eq. 2 and Eq. 3, Supplementary Section S-1):
+  1. draw m, a uniformly random permutation of the N columns;
+  2. for k = 1..N draw x_k from P(x_k | x_1..x_{k-1}; m), which is proportional
+     to |u_{x_k}^T h|^2, where u_y = U[y, (m_1..m_k)] is a k-dim row vector and h is
+     the k-dim normal vector orthogonal to u_{x_1}..u_{x_{k-1}} (Eq. 3);
+  3. h comes from Gaussian elimination carried out on the base rows in the full
+     N-dimensional space, each new base row being eliminated against the earlier
+     ones, followed by back substitution (Section S-1);
+  4. the inner products u_y^T h for all sites y give the weights (Section S-1: the
+     2Lk operations of step k).
+
+Readings of points the paper leaves open (each is listed in the design notes):
+  * m is drawn per sample (the identity of Eq. 2 averages over all permutations;
+    a fixed column order is biased).
+  * The normal vector is h = (h_1..h_{k-1}, 1): its normalisation cancels in the
+    conditional, so the last component is fixed to 1.
+  * Weights are computed for all L sites and set to exactly 0 on sites already
+    drawn (they are 0 in exact arithmetic).
+  * Inverse CDF: with C_y the running sum of the weights in site order and
+    Z = C_{L-1}, x_k = min{ y : C_y > u Z }; if rounding leaves no such y, the last
+    site with a nonzero weight is taken.
+  * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed lo32, seed hi32),
+    counter = (block, stream, sample lo32, sample hi32).  Stream 0 feeds a
+    Fisher-Yates shuffle of (0..N-1): block j serves shuffle steps i = N-1-2j (words
+    0, 1) and i = N-2-2j (words 2, 3), each taking r = word_a * 2^32 + word_b and
+    swapping m[i] with m[(r * (i+1)) >> 64].  Stream 1 block k gives the uniform of
+    step k (0-based): u = ((w0 >> 5) * 2^26 + (w1 >> 6)) * 2^-53.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+from scipy.linalg import solve_triangular
+
+MASK32 = 0xFFFFFFFF
+_PHILOX_M0 = 0xD2511F53
+_PHILOX_M1 = 0xCD9E8D57
+_PHILOX_W0 = 0x9E3779B9
+_PHILOX_W1 = 0xBB67AE85
+STREAM_PERM = 0
+STREAM_SITE = 1
+
+
+# --------------------------------------------------------------------------------------
+# Philox4x32-10, from its published definition (Salmon, Moraes, Dror, Shaw, SC'11).
+# --------------------------------------------------------------------------------------
+def philox4x32_10(ctr, key):
+    """Ten Philox4x32 rounds; the key is bumped by the Weyl constants between rounds."""
+    c0, c1, c2, c3 = (int(v) & MASK32 for v in ctr)
+    k0, k1 = (int(v) & MASK32 for v in key)
+    for rnd in range(10):
+        if rnd:
+            k0 = (k0 + _PHILOX_W0) & MASK32
+            k1 = (k1 + _PHILOX_W1) & MASK32
+        p0 = _PHILOX_M0 * c0
+        p1 = _PHILOX_M1 * c2
+        c0, c1, c2, c3 = ((p1 >> 32) ^ c1 ^ k0, p1 & MASK32, (p0 >> 32) ^ c3 ^ k1, p0 & MASK32)
+    return c0, c1, c2, c3
+
+
+def _key(seed: int):
+    seed = int(seed)
+    return (seed & MASK32, (seed >> 32) & MASK32)
+
+
+def _ctr(block: int, stream: int, sample: int):
+    sample = int(sample)
+    return (int(block) & MASK32, stream, sample & MASK32, (sample >> 32) & MASK32)
+
+
+def permutation(seed: int, sample: int, N: int) -> np.ndarray:
+    """The column order m of one sample (0-based), Fisher-Yates from Philox stream 0."""
+    m = list(range(N))
+    i = N - 1
+    block = 0
+    while i >= 1:
+        w = philox4x32_10(_ctr(block, STREAM_PERM, sample), _key(seed))
+        for hi, lo in ((w[0], w[1]), (w[2], w[3])):
+            if i < 1:
+                break
+            r = (hi << 32) | lo
+            j = (r * (i + 1)) >> 64
+            m[i], m[j] = m[j], m[i]
+            i -= 1
+        block += 1
+    return np.array(m, dtype=np.int64)
+
+
+def site_uniform(seed: int, sample: int, k: int) -> float:
+    """The uniform in [0, 1) used to draw x_k (k 0-based), 53 bits, Philox stream 1."""
+    w = philox4x32_10(_ctr(k, STREAM_SITE, sample), _key(seed))
+    return float(((w[0] >> 5) << 26) + (w[1] >> 6)) * 2.0**-53
+
+
+# --------------------------------------------------------------------------------------
+# The draw (main text after Eq. 2; tie rule as stated in the module header)
+# --------------------------------------------------------------------------------------
+def inverse_cdf(p: np.ndarray, u: float) -> int:
+    C = np.cumsum(p)
+    t = u * C[-1]
+    hit = np.nonzero(C > t)[0]
+    if hit.size:
+        return int(hit[0])
+    return int(np.nonzero(p > 0)[0][-1])
+
+
+# --------------------------------------------------------------------------------------
+# One sample, step by step (Eq. 2, Eq. 3, Section S-1)
+# --------------------------------------------------------------------------------------
+def sample_one(U, seed: int = 0, sample: int = 0, n_steps: int | None = None, m=None,
+               force_x=None, record: bool = False):
+    """Draw one configuration.
+
+    U        L x N orbitals (float64 or complex128), U^dagger U = 1.
+    n_steps  number of fermions to place (N by default; fewer gives the marginal of the
+             first n_steps positions, the paper's marginal-sampling case).
+    m        column order; drawn from Philox(seed, sample) when None.
+    force_x  teacher forcing: x_k is taken from force_x instead of being drawn (the
+             weights are still computed), used to compare conditionals step by step.
+    record   also return, per step, the normalised conditional over all L sites, the
+             normaliser Z_k, the pivot s_k = u_{x_k}^T h and the uniform u_k.
+
+    Returns a dict with 'x' (ordered, int64), 'm', and when record is set 'probs'
+    (n_steps x L), 'Z', 's', 'u', 'logp' (log of the chain's probability of x given m),
+    'hnorm2' (|h|^2 per step).
+    """
+    U = np.asarray(U)
+    L, N = U.shape
+    K = N if n_steps is None else int(n_steps)
+    dtype = np.result_type(U.dtype, np.float64)
+    m = permutation(seed, sample, N) if m is None else np.asarray(m, dtype=np.int64)
+    Ut = U[:, m].astype(dtype)            # row y restricted to the first k columns is u_y
+    E = np.zeros((N, N), dtype)           # base rows after elimination, full N-dim space
+    x: list[int] = []
+    rec = {"probs": [], "Z": [], "s": [], "u": [], "hnorm2": []}
+    logp = 0.0
+    for k in range(K):                    # k base rows x_0..x_{k-1} are fixed
+        if k >= 1:
+            # Eliminate the newest base row against the earlier ones (Section S-1):
+            # subtract the combination c of earlier echelon rows that zeroes its first
+            # k-1 entries, i.e. solve c E[:k-1, :k-1] = r[:k-1] (forward substitution).
+            r = Ut[x[k - 1], :].copy()
+            if k >= 2:
+                c = solve_triangular(E[: k - 1, : k - 1], r[: k - 1], trans="T", lower=False)
+                r = r - c @ E[: k - 1, :]
+                r[: k - 1] = 0.0
+            E[k - 1, :] = r
+        # Normal vector h in k+1 dims (Eq. 3): last entry 1, back substitution on the
+        # upper-triangular echelon rows for the first k entries.
+        h = np.zeros(k + 1, dtype)
+        h[k] = 1.0
+        if k:
+            h[:k] = solve_triangular(E[:k, :k], -E[:k, k], lower=False)
+        # Inner products u_y^T h for every site y (Section S-1).
+        v = Ut[:, : k + 1] @ h
+        p = np.abs(v) ** 2
+        if x:
+            p[np.array(x)] = 0.0
+        u = site_uniform(seed, sample, k)
+        if force_x is not None:
+            xk = int(force_x[k])
+        else:
+            xk = inverse_cdf(p, u)
+        Z = float(np.cumsum(p)[-1])
+        if record:
+            rec["probs"].append(p / Z)
+            rec["Z"].append(Z)
+            rec["s"].append(v[xk])
+            rec["u"].append(u)
+            rec["hnorm2"].append(float(np.sum(np.abs(h) ** 2)))
+        logp += math.log(p[xk] / Z) if p[xk] > 0 else -math.inf
+        x.append(xk)
+    out = {"x": np.array(x, dtype=np.int64), "m": m}
+    if record:
+        out["probs"] = np.array(rec["probs"])
+        out["Z"] = np.array(rec["Z"])
+        out["s"] = np.array(rec["s"])
+        out["u"] = np.array(rec["u"])
+        out["hnorm2"] = np.array(rec["hnorm2"])
+        out["logp"] = logp
+    return out
+
+
+def sample(U, B: int, seed: int = 0, first_sample_index: int = 0, n_steps: int | None = None):
+    """B configurations, sample b keyed by (seed, first_sample_index + b); B x n_steps int64."""
+    U = np.asarray(U)
+    K = U.shape[1] if n_steps is None else n_steps
+    out = np.zeros((B, K), dtype=np.int64)
+    for b in range(B):
+        out[b] = sample_one(U, seed, first_sample_index + b, n_steps=n_steps)["x"]
+    return out
+
+
+def _sample_range(args):
+    U, seed, lo, hi, n_steps = args
+    return [sample_one(U, seed, s, n_steps=n_steps)["x"] for s in range(lo, hi)]
+
+
+def sample_parallel(U, B: int, seed: int = 0, first_sample_index: int = 0, n_steps=None,
+                    workers: int | None = None):
+    """``sample`` over a spawn-started process pool (one single-threaded worker per core)."""
+    import multiprocessing as mp
+    import os
+
+    workers = workers or os.cpu_count() or 1
+    workers = max(1, min(workers, B))
+    bounds = np.linspace(first_sample_index, first_sample_index + B, workers + 1).astype(int)
+    jobs = [(U, seed, int(bounds[i]), int(bounds[i + 1]), n_steps) for i in range(workers)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers, initializer=_single_thread) as pool:
+        parts = pool.map(_sample_range, jobs)
+    return np.array([x for part in parts for x in part], dtype=np.int64)
+
+
+def _single_thread():
+    import os
+
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    try:
+        from threadpoolctl import threadpool_limits
+
+        threadpool_limits(1)
+    except Exception:
+        pass
+
+
+# --------------------------------------------------------------------------------------
+# Definitional tiers for tiny sizes
+# --------------------------------------------------------------------------------------
+def conditional_by_determinants(U, m, x_prefix) -> np.ndarray:
+    """Unnormalised conditional of step k = len(x_prefix) straight from its definition
+    (Eq. 2): |det U[(x_prefix, y), (m_1..m_{k+1})]|^2 for every site y."""
+    U = np.asarray(U)
+    L = U.shape[0]
+    k = len(x_prefix)
+    cols = np.asarray(m)[: k + 1]
+    p = np.zeros(L)
+    for y in range(L):
+        rows = list(x_prefix) + [y]
+        p[y] = abs(np.linalg.det(U[np.ix_(rows, cols)])) ** 2
+    return p
+
+
+def chain_probability(U, m, x) -> float:
+    """Probability that the chain with column order m produces the ordered tuple x."""
+    return math.exp(sample_one(U, m=m, force_x=x, record=True)["logp"])
+
+
+def target_ordered(U, x) -> float:
+    """Eq. 1: |det U_{x,n}|^2 / N! for an ordered tuple x."""
+    U = np.asarray(U)
+    N = U.shape[1]
+    return abs(np.linalg.det(U[np.asarray(x), :])) ** 2 / math.factorial(N)
+
+
+def set_probabilities(U) -> dict:
+    """Brute force over all C(L, N) site sets S: P(S) = |det U_S|^2 (sums to 1 by
+    Cauchy-Binet when U^dagger U = 1)."""
+    U = np.asarray(U)
+    L, N = U.shape
+    return {S: abs(np.linalg.det(U[list(S), :])) ** 2 for S in itertools.combinations(range(L), N)}
+
+
+def one_body_density(U) -> np.ndarray:
+    """rho(y) = sum_n |U_{y n}|^2, the expected occupation of site y (sums to N)."""
+    return np.sum(np.abs(np.asarray(U)) ** 2, axis=1)
+
+
+def pair_density(U) -> np.ndarray:
+    """rho2(y, z) = rho(y) rho(z) - |G(y, z)|^2 with G = U U^dagger (y != z): the
+    probability that both y and z are occupied."""
+    U = np.asarray(U)
+    G = U @ U.conj().T
+    rho = np.real(np.diag(G))
+    R = np.outer(rho, rho) - np.abs(G) ** 2
+    np.fill_diagonal(R, 0.0)
+    return R

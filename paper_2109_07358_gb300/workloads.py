@@ -1,0 +1,175 @@
+"""Seeded synthetic inputs for fast fermion sampling (arXiv 2109.07358).
+
+Every generator returns an L x N matrix U with orthonormal columns (U^dagger U = 1,
+the condition stated with Eq. 1), plus the sizes of the workload.  The module holds
+the inputs only: it contains none of the sampling arithmetic, so the CPU oracle and
+the CUDA path can both consume its outputs without sharing any of the method.
+
+Workloads (sizes are parameters; the defaults are the ones the tests and the bench use):
+
+* ``open_chain``      1D open chain, hopping -1: closed-form sine orbitals.
+* ``square_lattice``  nx x ny open square lattice, bond phases uniform in [0, 2 pi).
+* ``anderson_chain``  1D open Anderson chain, on-site energies uniform in [-W, W]
+                      (the Hamiltonian of Eq. 5, one spin species).
+* ``haar``            Haar-random orbitals: QR of a Gaussian matrix.
+* ``batch_sizes``     log-uniform (L, N) pairs for many independent instances.
+* ``lensemble_orbitals``  top-N left singular vectors of unit-norm Gaussian
+                      feature rows (stand-in for the sentence embeddings of the
+                      text-summarisation example; the real data is not available).
+* ``double_well``     the double-well chain of the supplementary double-well section.
+
+Matrices are float64 / complex128 and C-contiguous (row-major L x N).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(np.random.SeedSequence(int(seed)))
+
+
+def open_chain(L: int, N: int) -> np.ndarray:
+    """Lowest-N orbitals of H = -sum_j (c_j^+ c_{j+1} + h.c.) on an open chain of L sites.
+
+    phi_n(j) = sqrt(2/(L+1)) sin(pi n j / (L+1)), j = 1..L, n = 1..N; energies
+    -2 cos(pi n/(L+1)) are increasing in n, so columns are in energy order.
+    """
+    j = np.arange(1, L + 1)[:, None]
+    n = np.arange(1, N + 1)[None, :]
+    return np.ascontiguousarray(np.sqrt(2.0 / (L + 1)) * np.sin(np.pi * n * j / (L + 1)))
+
+
+def open_chain_hamiltonian(L: int) -> np.ndarray:
+    H = np.zeros((L, L))
+    i = np.arange(L - 1)
+    H[i, i + 1] = -1.0
+    H[i + 1, i] = -1.0
+    return H
+
+
+def square_lattice_hamiltonian(nx: int, ny: int, seed: int = 0) -> np.ndarray:
+    """Open nx x ny square lattice; bond (a, b) with a < b gets H_ab = -exp(i theta_ab),
+    H_ba = conj(H_ab), theta_ab ~ U[0, 2 pi).  Site index a = ix * ny + iy.  Bonds are
+    drawn in the order: all +x bonds (row-major over (ix, iy)), then all +y bonds."""
+    r = _rng(seed)
+    L = nx * ny
+    H = np.zeros((L, L), np.complex128)
+    ix, iy = np.meshgrid(np.arange(nx - 1), np.arange(ny), indexing="ij")
+    a = (ix * ny + iy).ravel()
+    b = ((ix + 1) * ny + iy).ravel()
+    jx, jy = np.meshgrid(np.arange(nx), np.arange(ny - 1), indexing="ij")
+    a2 = (jx * ny + jy).ravel()
+    b2 = (jx * ny + jy + 1).ravel()
+    A = np.concatenate([a, a2])
+    Bb = np.concatenate([b, b2])
+    theta = r.uniform(0.0, 2.0 * np.pi, size=A.size)
+    t = -np.exp(1j * theta)
+    H[A, Bb] = t
+    H[Bb, A] = np.conj(t)
+    return H
+
+
+def _lowest(H: np.ndarray, N: int) -> np.ndarray:
+    import scipy.linalg as sl
+
+    w, v = sl.eigh(H, subset_by_index=[0, N - 1], driver="evr")
+    return np.ascontiguousarray(v)
+
+
+def square_lattice(nx: int, ny: int, N: int, seed: int = 0) -> np.ndarray:
+    """Lowest-N orbitals (complex128, L = nx*ny) of ``square_lattice_hamiltonian``."""
+    return _lowest(square_lattice_hamiltonian(nx, ny, seed), N)
+
+
+def anderson_onsite(L: int, W: float = 1.0, seed: int = 0) -> np.ndarray:
+    return _rng(seed).uniform(-W, W, size=L)
+
+
+def anderson_chain(L: int, N: int, W: float = 1.0, seed: int = 0) -> np.ndarray:
+    """Lowest-N orbitals (real) of H = -sum_j (c_j^+ c_{j+1} + h.c.) + sum_j w_j n_j,
+    open boundaries, w_j ~ U[-W, W]."""
+    import scipy.linalg as sl
+
+    d = anderson_onsite(L, W, seed)
+    e = -np.ones(L - 1)
+    try:
+        w, v = sl.eigh_tridiagonal(d, e, select="i", select_range=(0, N - 1), lapack_driver="stemr")
+    except Exception:  # pragma: no cover - older LAPACK without stemr selection
+        H = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+        return _lowest(H, N)
+    return np.ascontiguousarray(v)
+
+
+def haar(L: int, N: int, seed: int = 0, complex_: bool = True) -> np.ndarray:
+    """Haar-random L x N orbitals: Q of the QR factorisation of an i.i.d. Gaussian matrix.
+    (Column phases are irrelevant: P(x) is invariant under U -> U D with D diagonal unitary.)"""
+    r = _rng(seed)
+    G = r.standard_normal((L, N))
+    if complex_:
+        G = G + 1j * r.standard_normal((L, N))
+    Q, _ = np.linalg.qr(G)
+    return np.ascontiguousarray(Q)
+
+
+def batch_sizes(n: int = 256, seed: int = 0, L_range=(256, 8192), N_max: int = 1024):
+    """n independent (L, N) pairs: L log-uniform in L_range, N log-uniform in
+    [16, min(N_max, L/4)]."""
+    r = _rng(seed)
+    out = []
+    for _ in range(n):
+        L = int(round(math.exp(r.uniform(math.log(L_range[0]), math.log(L_range[1])))))
+        hi = min(N_max, L // 4)
+        N = int(round(math.exp(r.uniform(math.log(16), math.log(hi)))))
+        out.append((L, max(1, min(N, hi))))
+    return out
+
+
+def lensemble_features(L: int, D: int, seed: int = 0) -> np.ndarray:
+    """L unit-norm Gaussian feature rows of dimension D (the b_i of the L-ensemble)."""
+    Phi = _rng(seed).standard_normal((L, D))
+    return Phi / np.linalg.norm(Phi, axis=1, keepdims=True)
+
+
+def lensemble_orbitals(Phi: np.ndarray, N: int) -> np.ndarray:
+    """Top-N eigenvectors of C = Phi Phi^T, taken as the left singular vectors of Phi
+    (thin SVD; the L x L kernel is never formed)."""
+    Uf, s, _ = np.linalg.svd(Phi, full_matrices=False)
+    return np.ascontiguousarray(Uf[:, :N])
+
+
+def lensemble_spectrum(Phi: np.ndarray):
+    """Eigen-decomposition of C = Phi Phi^T restricted to its rank: (lambda_j, u_j),
+    lambda descending, from the thin SVD of Phi."""
+    Uf, s, _ = np.linalg.svd(Phi, full_matrices=False)
+    return s**2, np.ascontiguousarray(Uf)
+
+
+def double_well(L: int = 64, N: int = 4, c: float = 89.929, a: float = 4096.0, b: float = 2.0,
+                t: float = math.pi**2 / 6) -> np.ndarray:
+    """Lowest-N orbitals of H = -t sum (c_i^+ c_{i+1} + h.c.) + sum_i V(x_i) n_i with
+    V(x) = a (x^2 - b)^2 - c x and x_i evenly spaced on [-2, 2] (supplementary
+    double-well section)."""
+    xs = np.linspace(-2.0, 2.0, L)
+    V = a * (xs**2 - b) ** 2 - c * xs
+    H = np.diag(V) - t * (np.eye(L, k=1) + np.eye(L, k=-1))
+    w, v = np.linalg.eigh(H)
+    return np.ascontiguousarray(v[:, :N]), xs
+
+
+# Named workloads with the sizes the tests and the bench use.
+def chain_L64_N8():
+    """1D open chain, L = 64, N = 8, real (the small plain FP64 workload)."""
+    return open_chain(64, 8)
+
+
+def lattice_64x64_N1024(seed: int = 0):
+    """64 x 64 open square lattice with random U(1) hopping phases, N = 1024, complex."""
+    return square_lattice(64, 64, 1024, seed)
+
+
+def anderson_L16384_N2048(seed: int = 0):
+    """1D Anderson chain L = 16384, w_j ~ U[-1, 1], N = 2048, real."""
+    return anderson_chain(16384, 2048, 1.0, seed)
