@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the fast-fermion-sampling hot path (arXiv 2109.07358) on GB300.
+
+A step is one ffs_sample call: the whole chain (permutations, N residual steps, N
+draw + state-update steps) over one batch of B samples of the workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ffs|reference]
+
+Default workload: 64 x 64 open square lattice with random U(1) hopping phases
+(L = 4096), the N = 1024 lowest orbitals (complex), B = 4096 samples, seed 0.
+Prints one JSON line (rank 0).  Under torchrun each rank samples its own index
+range (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "lattice64x64_N1024_B4096": dict(
+        make="lattice", B=4096, L=4096, N=1024, cplx=True,
+        desc="64x64 open square lattice, random U(1) hopping phases (seed 0), N=1024 lowest orbitals, "
+             "complex, B=4096 samples, Philox seed 0"),
+    "chain64_N8_B10000": dict(
+        make="chain", B=10000, L=64, N=8, cplx=False,
+        desc="1D open chain L=64, N=8 (closed-form orbitals), B=10^4 samples, Philox seed 0"),
+}
+
+# Peak denominators (GB300).  FP64 and FP32 CUDA-core rates: nominal unit counts x
+# clock (FP64: 1.25 TFLOP/s dense nominal; FP32: 152 SMs x 128 lanes x 2 flops x 2.07 GHz).
+NOMINAL_FP64_TFLOPS = 1.25
+NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_sus=d["bf16_tflops_sustained"],
+                    source="measured")
+    return dict(hbm_gbs=6800.0, bf16=1900.0, bf16_sus=1700.0, source="fallback")
+
+
+def make_U(spec):
+    from paper_2109_07358_gb300 import workloads as w
+
+    if spec["make"] == "lattice":
+        return w.lattice_64x64_N1024(0)
+    if spec["make"] == "chain":
+        return w.chain_L64_N8()
+    raise ValueError(spec["make"])
+
+
+def flops_per_sample(L, N, cplx):
+    """Algorithmic residual flops per sample: the paper's 2Lk per step summed over
+    k = 1..N, i.e. L N (N+1) real flops (x4 for complex arithmetic)."""
+    return L * N * (N + 1) * (4 if cplx else 1)
+
+
+def tail_flops_per_sample(N, cplx):
+    """Arithmetic of the per-sample Gauss-Jordan state update as implemented: at step k
+    (0-based, k < N-1) a k x (N-k) product of the new row with the state and a
+    k x (N-k-1) rank-1 update, 2 real flops per real multiply-add (8 per complex)."""
+    k = np.arange(N - 1, dtype=np.float64)
+    macs = float(np.sum(k * (N - k) + k * (N - k - 1)))
+    return macs * (8 if cplx else 2)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def _oracle_worker(args):
+    U, seed, lo, hi = args
+    from oracle import ffs_oracle as o
+
+    o._single_thread()
+    t = time.perf_counter()
+    for s in range(lo, hi):
+        o.sample_one(U, seed, s)
+    return time.perf_counter() - t
+
+
+def oracle_baseline(U, n_samples, seed=0, workers=None):
+    """Time the CPU oracle (as it stands) on n_samples of the workload, one
+    single-threaded worker process per core (spawn)."""
+    import multiprocessing as mp
+
+    workers = max(1, min(workers or os.cpu_count() or 1, n_samples))
+    bounds = np.linspace(0, n_samples, workers + 1).astype(int)
+    jobs = [(U, seed, int(bounds[i]), int(bounds[i + 1])) for i in range(workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        pool.map(_oracle_worker, [(U[:8, :2].copy() / np.linalg.norm(U[:8, :2], axis=0), 0, 0, 1)] * workers)
+        t0 = time.perf_counter()
+        pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t0
+    return n_samples / wall, wall, workers
+
+
+def run_reference(args, spec, rank, world):
+    """--impl reference: the CPU oracle on the host cores, same metric and workload."""
+    if rank != 0:
+        return 0
+    U = make_U(spec)
+    n = args.ref_samples or max(2, (os.cpu_count() or 1))
+    for _ in range(args.warmup):
+        oracle_baseline(U, max(1, n // 4))
+    rates = []
+    walls = []
+    for _ in range(args.steps):
+        r, wall, workers = oracle_baseline(U, n)
+        rates.append(r)
+        walls.append(wall)
+    v = float(np.median(rates))
+    out = {
+        "impl": "reference", "metric": "FFS samples/s", "value": v, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(walls)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"], "B_per_step": n,
+                   "sample": f"{n} samples of the workload per step (indices 0..{n - 1})"},
+        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": workers, "kind": "oracle",
+                         "sample": f"{n} samples per step, one single-threaded worker per core"},
+        "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU path
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ffs", choices=["ffs", "reference"])
+    ap.add_argument("--workload", default="lattice64x64_N1024_B4096", choices=list(WORKLOADS))
+    ap.add_argument("--B", type=int, default=0, help="override samples per step")
+    ap.add_argument("--chosen", default="bf16x3", choices=["bf16x3", "fp32", "tf32", "bf16"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-samples", type=int, default=0)
+    args = ap.parse_args()
+    spec = dict(WORKLOADS[args.workload])
+    if args.B:
+        spec["B"] = args.B
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, spec, rank, world)
+
+    import torch
+
+    from paper_2109_07358_gb300 import build as _build
+    from paper_2109_07358_gb300 import ffs
+
+    _build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    peaks = load_peaks()
+    U_np = make_U(spec)
+    L, N = U_np.shape
+    cplx = np.iscomplexobj(U_np)
+    B = spec["B"]
+    U = torch.from_numpy(U_np).cuda()
+    res_flag = {"bf16x3": ffs.FFS_RES_BF16X3, "fp32": ffs.FFS_RES_FP32, "tf32": ffs.FFS_RES_TF32,
+                "bf16": ffs.FFS_RES_BF16}[args.chosen]
+    flags = res_flag | ffs.FFS_STATE_FP64
+    stream = torch.cuda.Stream()
+    S = ffs.Sampler(U, flags, stream=stream)
+    x = torch.empty((B, N), dtype=torch.int32, device="cuda")
+    first = rank * B * (args.steps + args.warmup + 1)
+
+    def step(i):
+        ffs.ffs_sample_ex(S.h, B, 0, first + i * B, 0, x, stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    S.sync()
+    ffs.ffs_profile(S.h, True)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            step(args.warmup + i)
+        ev1.record(stream)
+        S.sync()
+        wall = time.perf_counter() - t0
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    prof = ffs.ffs_profile_read(S.h)
+    ffs.ffs_profile(S.h, False)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * B / (ms_step / 1e3)
+
+    # per-phase roofline
+    res_ms, res_n = prof["residual"]
+    tail_ms, tail_n = prof["tail"]
+    perm_ms, perm_n = prof["perm"]
+    res_flops = flops_per_sample(L, N, cplx) * B * args.steps
+    issued = 2 * (2 * L) * (2 * N) * N * B * args.steps if cplx else 2 * L * N * N * B * args.steps
+    tail_fl = tail_flops_per_sample(N, cplx) * B * args.steps
+    mult = {"bf16x3": 3, "fp32": 1, "tf32": 1, "bf16": 1}[args.chosen]
+    if args.chosen == "fp32":
+        res_peak, res_unit, res_bound = NOMINAL_FP32_TFLOPS, "TFLOP/s", "alu"
+    elif args.chosen == "tf32":
+        res_peak, res_unit, res_bound = peaks["bf16_sus"] / 2, "TFLOP/s", "tensor"
+    else:
+        res_peak, res_unit, res_bound = peaks["bf16_sus"] / mult, "TFLOP/s", "tensor"
+    phases = {
+        "residual": {"ms": res_ms / args.steps, "launches_per_step": res_n / args.steps,
+                     "algorithmic_tflops": res_flops / (res_ms / 1e3) / 1e12 if res_ms else None,
+                     "issued_tflops": issued * mult / (res_ms / 1e3) / 1e12 if res_ms else None},
+        "tail": {"ms": tail_ms / args.steps, "launches_per_step": tail_n / args.steps,
+                 "fp64_tflops": tail_fl / (tail_ms / 1e3) / 1e12 if tail_ms else None},
+        "perm": {"ms": perm_ms / args.steps, "launches_per_step": perm_n / args.steps},
+    }
+    dominant = "tail" if tail_ms >= res_ms else "residual"
+    if dominant == "tail":
+        ach = tail_fl / (tail_ms / 1e3) / 1e12
+        roof = {"kernel": "tail (draw + FP64 state update)", "bound": "alu", "achieved": ach,
+                "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / NOMINAL_FP64_TFLOPS,
+                "traffic": None, "peak_source": "nominal FP64 rate (1.25 TFLOP/s)"}
+    else:
+        ach = res_flops / (res_ms / 1e3) / 1e12
+        roof = {"kernel": f"residual ({args.chosen})", "bound": res_bound, "achieved": ach, "peak": res_peak,
+                "unit": res_unit, "frac": ach / res_peak, "traffic": None,
+                "peak_source": f"{peaks['source']} bf16 sustained / {mult}" if res_bound == "tensor"
+                else "nominal FP32 rate"}
+
+    out = {
+        "metric": "FFS samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64" if cplx else "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"], "L": L, "N": N, "B": B,
+                   "form": f"batched {args.chosen} residual + FP64 state", "l2": "inputs larger than L2 "
+                   "(the per-sample state of a batch is tens of GB)"},
+        "clocks": clk.summary(),
+        "gpu_launches": int(res_n + tail_n + perm_n) // args.steps,
+        "roofline": roof,
+        "phases": phases,
+    }
+
+    if not args.no_plain and rank == 0:
+        P = ffs.Sampler(U, ffs.FFS_FORM_PLAIN, stream=stream)
+        xp = torch.empty((B, N), dtype=torch.int32, device="cuda")
+        ffs.ffs_sample_ex(P.h, min(B, 64), 0, 0, 0, xp, stream=stream)
+        P.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ffs.ffs_sample_ex(P.h, B, 0, 0, 0, xp, stream=stream)
+        e1.record(stream)
+        P.sync()
+        pms = e0.elapsed_time(e1)
+        out["plain"] = {"value": B / (pms / 1e3), "unit": "samples/s", "ms_per_step": pms,
+                        "form": "plain per-sample FP32 (CUDA cores, FP32 state)",
+                        "chosen_over_plain": value / world / (B / (pms / 1e3))}
+        P.close()
+
+    if not args.no_e2e:
+        # End to end through the C ABI with host buffers: U uploaded from pinned host
+        # memory (ffs_create_ex), samples read back into pinned host memory.
+        U_host = torch.from_numpy(U_np).pin_memory()
+        x_host = torch.empty((B, N), dtype=torch.int32).pin_memory()
+        times = []
+        for i in range(args.steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = ffs.ffs_create_ex(U_host, ffs.dtype_of(U_host), L, N, N, flags, stream)
+            ffs.ffs_sample_ex(h, B, 0, first + i * B, 0, x_host, stream=stream)
+            ffs.ffs_destroy(h)
+            times.append(time.perf_counter() - t0)
+        e2e_s = float(np.median(times[1:]))
+        out["e2e"] = {"value": world * B / e2e_s, "unit": "samples/s",
+                      "h2d_bytes_per_step": int(U_host.numel() * U_host.element_size()),
+                      "d2h_bytes_per_step": int(x_host.numel() * 4)}
+
+    if not args.no_cpu and rank == 0:
+        n = max(2, os.cpu_count() or 1)
+        rate, wall, workers = oracle_baseline(U_np, n)
+        out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": workers, "kind": "oracle",
+                               "sample": f"{n} samples of the same workload (indices 0..{n - 1}), "
+                                         f"{wall:.1f} s wall"}
+
+    S.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * ffs.h - C ABI of the GB300 fast-fermion-sampling library (libffs.so).
+ *
+ * Fast fermion sampling (FFS), Sun, Zou & Li, arXiv 2109.07358.  Given an L x N
+ * matrix U with orthonormal columns (U^dagger U = 1), draw ordered configurations
+ * x = (x_1..x_N), x_j in {0..L-1}, from P(x) = |det U_{x,n}|^2 / N!   (Eq. 1).
+ * Each sample draws its own uniformly random column order m and then places one
+ * fermion per step k by the chain rule (Eq. 2); the conditional weight of site y at
+ * step k is |u_y^T h|^2 with h the normal vector of Eq. 3, evaluated for all L sites
+ * at once (Supplementary Section S-1).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an ffs_status; FFS_OK is 0.  The message of the last error
+ *     of a handle is ffs_last_error(handle).
+ *   - Sites and columns are 0-based (the paper is 1-based).  Matrices are row-major.
+ *   - Pointers may be host or device memory unless stated; the library tells them
+ *     apart with cudaPointerGetAttributes.  Host output buffers are written before
+ *     the call returns; device output buffers are written in stream order.
+ *   - Sample b of a call is fully determined by (U, seed, first_sample_index + b,
+ *     the precision flags): it does not depend on B, on how a batch is split into
+ *     waves, or on other work sharing the GPU.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key (seed lo32,
+ *     seed hi32) and counter (block, stream, sample lo32, sample hi32).  Stream 0
+ *     drives a Fisher-Yates shuffle that gives m; stream 1, block k gives the
+ *     53-bit uniform of step k.
+ *   - Device-detected numeric failures (a non-finite or non-positive normaliser, a
+ *     vanishing pivot) are recorded in a status word that ffs_sync returns.
+ *   - Nothing here traps or hangs the GPU: every device-side wait is bounded and
+ *     reports FFS_E_TIMEOUT instead.
+ */
+#ifndef FFS_H
+#define FFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ffs_ctx* ffs_handle;
+
+typedef enum {
+  FFS_OK = 0,
+  FFS_E_ARG = 1,              /* invalid argument (sizes, null pointers, flags)        */
+  FFS_E_NOT_ORTHONORMAL = 2,  /* max |U^dagger U - 1| above the tolerance (Eq. 1 text)  */
+  FFS_E_NOMEM = 3,            /* device allocation failed or budget exceeded            */
+  FFS_E_CUDA = 4,             /* a CUDA runtime call failed (message in ffs_last_error) */
+  FFS_E_NUMERIC = 5,          /* normaliser <= 0 or non-finite, or |pivot|^2 < 1e-300   */
+  FFS_E_TIMEOUT = 6,          /* a bounded wait ran out                                 */
+  FFS_E_BUSY = 7,             /* the engine cannot take the request now                 */
+  FFS_E_UNSUPPORTED = 8       /* option not available in this build / on this device    */
+} ffs_status;
+
+/* Element type of U as passed to ffs_create_ex. */
+typedef enum {
+  FFS_F64 = 0,   /* double, L x N                        */
+  FFS_C128 = 1,  /* interleaved (re, im) double pairs    */
+  FFS_F32 = 2,   /* float                                */
+  FFS_C64 = 3    /* interleaved (re, im) float pairs     */
+} ffs_dtype;
+
+/* Flags of ffs_create_ex (bitwise OR of one value from each group).
+ *
+ * Residual arithmetic (the all-site inner products u_y^T h of step k):
+ *   FFS_RES_FP32    FP32 CUDA-core arithmetic                 (the "FP32 path")
+ *   FFS_RES_BF16X3  tensor cores, operands split into BF16 hi+lo, three products
+ *                   hi*hi + hi*lo + lo*hi, FP32 accumulation   (default)
+ *   FFS_RES_BF16    tensor cores, one BF16 product, FP32 accumulation
+ *   FFS_RES_TF32    tensor cores, one TF32 product, FP32 accumulation
+ * Per-sample elimination state (the normal vector h, the pivots):
+ *   FFS_STATE_FP64  IEEE double                                 (default)
+ *   FFS_STATE_FP32  IEEE float (used by the plain form)
+ * Form:
+ *   FFS_FORM_BATCHED  all samples of a wave share one contraction per step (default)
+ *   FFS_FORM_PLAIN    the plain per-sample form: per sample, an FP32 CUDA-core
+ *                     product with the columns U[:, m_1..m_k] and an FP32 state
+ * Checks:
+ *   FFS_NO_ORTHO_CHECK  skip the U^dagger U = 1 check in ffs_create_ex
+ */
+#define FFS_RES_BF16X3 0x0u
+#define FFS_RES_FP32 0x1u
+#define FFS_RES_BF16 0x2u
+#define FFS_RES_TF32 0x3u
+#define FFS_RES_MASK 0xFu
+#define FFS_STATE_FP64 0x00u
+#define FFS_STATE_FP32 0x10u
+#define FFS_STATE_MASK 0xF0u
+#define FFS_FORM_BATCHED 0x000u
+#define FFS_FORM_PLAIN 0x100u
+#define FFS_FORM_MASK 0xF00u
+#define FFS_NO_ORTHO_CHECK 0x1000u
+
+/* Tolerance of the orthonormality check: max_ij |(U^dagger U)_ij - delta_ij|. */
+#define FFS_ORTHO_TOL 1e-6
+
+/*
+ * ffs_create - set up a sampler for one U (Eq. 1: L x N, U^dagger U = 1).
+ *   U     real FP64, row-major L x N (leading dimension N), host or device memory.
+ *         The library copies it; the caller keeps ownership and may free it on return.
+ *   L, N  1 <= N <= L.
+ *   out   receives the handle (owning all device memory it allocates).
+ * Equivalent to ffs_create_ex(U, FFS_F64, L, N, N, 0, NULL, out).  Synchronous.
+ * Errors: FFS_E_ARG, FFS_E_NOT_ORTHONORMAL, FFS_E_NOMEM, FFS_E_CUDA.
+ */
+int ffs_create(const double* U, int64_t L, int64_t N, ffs_handle* out);
+
+/*
+ * ffs_create_ex - as ffs_create with an element type, a leading dimension ldU >= N
+ * (in elements), flags (above) and a CUDA stream (cudaStream_t, NULL = legacy default
+ * stream) on which every later call of this handle is ordered.
+ */
+int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, unsigned flags,
+                  void* cuda_stream, ffs_handle* out);
+
+/*
+ * ffs_sample - draw B configurations (Eq. 1 via the chain of Eq. 2-3).
+ *   B      number of samples, B >= 0 (B = 0 is a no-op).
+ *   seed   Philox key; sample b uses sample index b.
+ *   out_x  B x N int32, row-major, sites in draw order (x_1..x_N); host or device.
+ * Asynchronous on the handle's stream when out_x is device memory; device-detected
+ * errors surface at ffs_sync or at the next call.
+ */
+int ffs_sample(ffs_handle h, int64_t B, uint64_t seed, int32_t* out_x);
+
+/*
+ * ffs_sample_ex - ffs_sample with options.
+ *   first_sample_index  sample b uses index first_sample_index + b (disjoint index
+ *                       ranges give independent samples; this is how a job is sharded).
+ *   n_steps             fermions to place, 1..N (N = the full configuration; fewer
+ *                       gives the marginal of the first n_steps positions, the
+ *                       paper's marginal-sampling case).  0 means N.
+ *   out_x               B x n_steps int32 (host or device).
+ *   out_perm            nullable; B x N int32 column orders m.
+ *   out_logp            nullable; B doubles, log of the chain's probability of x
+ *                       given m (sum over steps of log(|s_k|^2 / Z_k)).
+ *   force_x             nullable; B x n_steps int32 teacher-forcing sites: step k
+ *                       places force_x[b][k] instead of drawing (weights are still
+ *                       evaluated).  Used to compare conditionals step by step.
+ *   out_probs           nullable; B x n_steps x L float32, the normalised conditional
+ *                       of every step (debug/parity output; large).
+ *   cuda_stream         NULL = the handle's stream.
+ */
+int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_index,
+                  int64_t n_steps, int32_t* out_x, int32_t* out_perm, double* out_logp,
+                  const int32_t* force_x, float* out_probs, void* cuda_stream);
+
+/* ffs_sync - wait for the handle's stream; return and clear the device status word. */
+int ffs_sync(ffs_handle h);
+
+/* ffs_last_error - message of the last failed call on h (never NULL; h may be NULL). */
+const char* ffs_last_error(ffs_handle h);
+
+/* ffs_destroy - release everything the handle owns.  NULL-safe. */
+void ffs_destroy(ffs_handle h);
+
+/* ffs_query - sizes and settings of a handle: L, N, dtype, flags, and the device bytes
+ * a batch of B samples needs (the per-sample state, the operands, the buffers). */
+int ffs_query(ffs_handle h, int64_t* L, int64_t* N, int* dtype, unsigned* flags,
+              int64_t B, int64_t* bytes_for_B);
+
+/* Phases reported by ffs_profile_read. */
+#define FFS_PHASE_PERM 0      /* column orders m and the step-0 operand              */
+#define FFS_PHASE_RESIDUAL 1  /* all-site weights |u_y^T h|^2 (Section S-1 products) */
+#define FFS_PHASE_TAIL 2      /* draw, pivot and elimination-state update            */
+#define FFS_NUM_PHASES 3
+
+/*
+ * ffs_profile - enable (1) or disable (0) per-phase timing of h: every kernel launch
+ * of h is bracketed by two CUDA events on its stream.  Enabling clears the totals.
+ * ffs_profile_read - synchronise, fold the recorded events into per-phase totals and
+ * return them: ms[p] total device milliseconds and launches[p] kernel launches of phase
+ * p since profiling was enabled (arrays of n entries, n <= FFS_NUM_PHASES).
+ */
+int ffs_profile(ffs_handle h, int enable);
+int ffs_profile_read(ffs_handle h, double* ms, int64_t* launches, int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFS_H */

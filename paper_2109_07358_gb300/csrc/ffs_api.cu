@@ -1,0 +1,472 @@
+// libffs C ABI: handle lifecycle, memory, and the per-step launch sequence.
+// The declarations and the contract of every entry point are in include/ffs.h.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "ffs_kernels.cuh"
+#include "ffs_residual_tc.cuh"
+
+using namespace fermi;
+
+static thread_local std::string g_null_handle_error;
+
+static int fail(ffs_ctx* c, int code, const std::string& msg) {
+  if (c)
+    c->last_error = msg;
+  else
+    g_null_handle_error = msg;
+  return code;
+}
+
+#define FFS_CUDA_TRY(ctx, expr)                                                                 \
+  do {                                                                                          \
+    cudaError_t _e = (expr);                                                                    \
+    if (_e != cudaSuccess)                                                                      \
+      return fail((ctx), _e == cudaErrorMemoryAllocation ? FFS_E_NOMEM : FFS_E_CUDA,            \
+                  std::string(#expr) + ": " + cudaGetErrorString(_e));                          \
+  } while (0)
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+static int op_mode_of(unsigned flags) {
+  if ((flags & FFS_FORM_MASK) == FFS_FORM_PLAIN) return kOpNone;
+  switch (flags & FFS_RES_MASK) {
+    case FFS_RES_FP32: return kOpF32;
+    case FFS_RES_BF16X3: return kOpBF16x3;
+    case FFS_RES_BF16: return kOpBF16;
+    case FFS_RES_TF32: return kOpTF32;
+  }
+  return -1;
+}
+
+static size_t op_elem_bytes(int op) {
+  switch (op) {
+    case kOpF32:
+    case kOpTF32: return 4;
+    case kOpBF16x3: return 4;  // two BF16 planes
+    case kOpBF16: return 2;
+    default: return 0;
+  }
+}
+
+static bool state_fp64(const ffs_ctx* c) { return (c->flags & FFS_STATE_MASK) == FFS_STATE_FP64; }
+
+static size_t state_elem_bytes(const ffs_ctx* c) {
+  return (c->cplx ? 2 : 1) * (state_fp64(c) ? sizeof(double) : sizeof(float));
+}
+
+// Device bytes per sample of a wave (not counting optional outputs).
+static size_t per_sample_bytes(const ffs_ctx* c) {
+  const int op = op_mode_of(c->flags);
+  size_t b = 0;
+  b += (size_t)c->N * 4;                           // m
+  b += (size_t)c->ldMask * 4;                      // mask
+  b += (size_t)c->Kp * op_elem_bytes(op);          // operand planes
+  b += (size_t)c->ldP * 4;                         // weights
+  b += (size_t)c->N * c->N * state_elem_bytes(c);  // elimination state
+  b += 8;                                          // logp
+  return b;
+}
+
+static void free_workspace(ffs_ctx* c) {
+  cudaFree(c->m);
+  cudaFree(c->mask);
+  cudaFree(c->H);
+  cudaFree(c->P);
+  cudaFree(c->W);
+  cudaFree(c->logp);
+  c->m = nullptr;
+  c->mask = nullptr;
+  c->H = nullptr;
+  c->P = nullptr;
+  c->W = nullptr;
+  c->logp = nullptr;
+  c->ws_B = 0;
+}
+
+static int ensure_workspace(ffs_ctx* c, int64_t Bw) {
+  if (Bw <= c->ws_B) return FFS_OK;
+  cudaStreamSynchronize(c->stream);
+  free_workspace(c);
+  const int op = op_mode_of(c->flags);
+  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->m, (size_t)Bw * c->N * 4));
+  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->mask, (size_t)Bw * c->ldMask * 4));
+  if (op != kOpNone) FFS_CUDA_TRY(c, cudaMalloc(&c->H, (size_t)Bw * c->Kp * op_elem_bytes(op)));
+  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->P, (size_t)Bw * c->ldP * 4));
+  FFS_CUDA_TRY(c, cudaMalloc(&c->W, (size_t)Bw * c->N * c->N * state_elem_bytes(c)));
+  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->logp, (size_t)Bw * 8));
+  c->ws_B = Bw;
+  return FFS_OK;
+}
+
+static void release(ffs_ctx* c) {
+  if (!c) return;
+  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  free_workspace(c);
+  cudaFree(c->U64);
+  cudaFree(c->Ue32);
+  cudaFree(c->Ue_hi);
+  cudaFree(c->Ue_lo);
+  cudaFree(c->Ue_tf32);
+  cudaFree(c->UT32);
+  cudaFree(c->status);
+  if (c->status_host) cudaFreeHost(c->status_host);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+// Widen a (possibly strided, host or device) U of any supported dtype into the
+// contiguous FP64 copy.
+__global__ void widen_kernel(const void* src, int dtype, int64_t L, int64_t N, int64_t ld, void* dst) {
+  const int64_t total = L * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = e / N, c = e % N;
+    switch (dtype) {
+      case FFS_F64: ((double*)dst)[e] = ((const double*)src)[y * ld + c]; break;
+      case FFS_F32: ((double*)dst)[e] = ((const float*)src)[y * ld + c]; break;
+      case FFS_C128: ((cd*)dst)[e] = ((const cd*)src)[y * ld + c]; break;
+      case FFS_C64: {
+        const cf v = ((const cf*)src)[y * ld + c];
+        ((cd*)dst)[e] = cd{v.re, v.im};
+        break;
+      }
+    }
+  }
+}
+
+// Per-phase CUDA-event timing (enabled by ffs_profile).
+static void prof_begin(ffs_ctx* c, int phase, cudaStream_t st) {
+  if (!c->prof) return;
+  while (c->ev_pool.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev_pool.push_back(e);
+  }
+  cudaEventRecord(c->ev_pool[c->ev_used], st);
+  c->prof_phase.push_back(phase);
+}
+static void prof_end(ffs_ctx* c, cudaStream_t st) {
+  if (!c->prof) return;
+  cudaEventRecord(c->ev_pool[c->ev_used + 1], st);
+  c->ev_used += 2;
+}
+static void prof_fold(ffs_ctx* c) {
+  for (size_t i = 0; i < c->prof_phase.size(); ++i) {
+    float ms = 0.f;
+    cudaEventSynchronize(c->ev_pool[2 * i + 1]);
+    cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]);
+    c->prof_ms[c->prof_phase[i]] += ms;
+    c->prof_launches[c->prof_phase[i]] += 1;
+  }
+  c->prof_phase.clear();
+  c->ev_used = 0;
+}
+
+#define TIMED(ctx, phase, st, expr)                                                             \
+  do {                                                                                          \
+    prof_begin((ctx), (phase), (st));                                                           \
+    cudaError_t _e2 = (expr);                                                                   \
+    prof_end((ctx), (st));                                                                      \
+    if (_e2 != cudaSuccess)                                                                     \
+      return fail((ctx), FFS_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e2));     \
+  } while (0)
+
+extern "C" {
+
+const char* ffs_last_error(ffs_handle h) {
+  return h ? h->last_error.c_str() : g_null_handle_error.c_str();
+}
+
+int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, unsigned flags,
+                  void* cuda_stream, ffs_handle* out) {
+  if (!out) return fail(nullptr, FFS_E_ARG, "ffs_create_ex: out is NULL");
+  *out = nullptr;
+  if (!U) return fail(nullptr, FFS_E_ARG, "ffs_create_ex: U is NULL");
+  if (dtype < FFS_F64 || dtype > FFS_C64) return fail(nullptr, FFS_E_ARG, "ffs_create_ex: bad dtype");
+  if (N < 1 || L < N) return fail(nullptr, FFS_E_ARG, "ffs_create_ex: need 1 <= N <= L");
+  if (ldU < N) return fail(nullptr, FFS_E_ARG, "ffs_create_ex: need ldU >= N");
+  if (L > (int64_t)1 << 30) return fail(nullptr, FFS_E_ARG, "ffs_create_ex: L too large");
+  const bool cplx = (dtype == FFS_C128 || dtype == FFS_C64);
+  if ((flags & FFS_FORM_MASK) == FFS_FORM_PLAIN)
+    flags = (flags & ~(FFS_RES_MASK | FFS_STATE_MASK)) | FFS_RES_FP32 | FFS_STATE_FP32;
+  if ((flags & FFS_FORM_MASK) > FFS_FORM_PLAIN || (flags & FFS_STATE_MASK) > FFS_STATE_FP32 ||
+      (flags & ~(FFS_RES_MASK | FFS_STATE_MASK | FFS_FORM_MASK | FFS_NO_ORTHO_CHECK)) ||
+      op_mode_of(flags) < 0)
+    return fail(nullptr, FFS_E_ARG, "ffs_create_ex: bad flags");
+
+  ffs_ctx* c = new ffs_ctx();
+  c->L = L;
+  c->N = N;
+  c->dtype = dtype;
+  c->cplx = cplx;
+  c->flags = flags;
+  c->stream = (cudaStream_t)cuda_stream;
+  const size_t smem_need = tail_smem_bytes(N, cplx, state_fp64(c));
+  if (smem_need > 224 * 1024) {
+    int r = fail(nullptr, FFS_E_UNSUPPORTED, "ffs_create_ex: N too large for the per-sample state kernel");
+    release(c);
+    return r;
+  }
+#define CREATE_TRY(expr)                                                                            \
+  do {                                                                                              \
+    cudaError_t _e = (expr);                                                                        \
+    if (_e != cudaSuccess) {                                                                        \
+      int r = fail(nullptr, _e == cudaErrorMemoryAllocation ? FFS_E_NOMEM : FFS_E_CUDA,             \
+                   std::string(#expr) + ": " + cudaGetErrorString(_e));                             \
+      release(c);                                                                                   \
+      return r;                                                                                     \
+    }                                                                                               \
+  } while (0)
+  CREATE_TRY(cudaGetDevice(&c->device));
+  CREATE_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  static bool configured = false;
+  if (!configured) {
+    CREATE_TRY(configure_kernels(N, cplx));
+    CREATE_TRY(configure_residual_tc());
+    configured = true;
+  }
+  c->Lr = cplx ? 2 * L : L;
+  c->Kr = cplx ? 2 * N : N;
+  c->Kp = round_up(c->Kr, 64);
+  c->Lrp = round_up(c->Lr, 256);
+  c->ldP = round_up(L, 4);
+  c->ldMask = (L + 31) / 32;
+
+  // FP64 copy of U
+  const size_t es64 = cplx ? sizeof(cd) : sizeof(double);
+  const size_t es_in = (dtype == FFS_F64) ? 8 : (dtype == FFS_C128) ? 16 : (dtype == FFS_F32) ? 4 : 8;
+  CREATE_TRY(cudaMalloc(&c->U64, (size_t)L * N * es64));
+  if ((dtype == FFS_F64 || dtype == FFS_C128) && ldU == N) {
+    CREATE_TRY(cudaMemcpyAsync(c->U64, U, (size_t)L * N * es64, cudaMemcpyDefault, c->stream));
+  } else {
+    void* stage = nullptr;
+    CREATE_TRY(cudaMalloc(&stage, (size_t)L * N * es_in));
+    cudaError_t e = cudaMemcpy2DAsync(stage, N * es_in, U, ldU * es_in, N * es_in, L, cudaMemcpyDefault,
+                                      c->stream);
+    if (e == cudaSuccess) {
+      widen_kernel<<<4 * c->num_sms, 256, 0, c->stream>>>(stage, dtype, L, N, N, c->U64);
+      e = cudaGetLastError();
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(stage);
+    CREATE_TRY(e);
+  }
+  if (!(flags & FFS_NO_ORTHO_CHECK)) {
+    double dev = 0.0;
+    CREATE_TRY(launch_ortho_check(c->U64, cplx, L, N, &dev, c->stream));
+    if (!(dev <= FFS_ORTHO_TOL)) {
+      char msg[160];
+      snprintf(msg, sizeof msg, "ffs_create_ex: U^dagger U deviates from 1 by %.3e (tolerance %.1e)", dev,
+               FFS_ORTHO_TOL);
+      int r = fail(nullptr, FFS_E_NOT_ORTHONORMAL, msg);
+      release(c);
+      return r;
+    }
+  }
+  const int op = op_mode_of(flags);
+  const size_t emb = (size_t)c->Lrp * c->Kp;
+  if (op == kOpF32) CREATE_TRY(cudaMalloc((void**)&c->Ue32, emb * 4));
+  if (op == kOpBF16x3 || op == kOpBF16) CREATE_TRY(cudaMalloc((void**)&c->Ue_hi, emb * 2));
+  if (op == kOpBF16x3) CREATE_TRY(cudaMalloc((void**)&c->Ue_lo, emb * 2));
+  if (op == kOpTF32) CREATE_TRY(cudaMalloc((void**)&c->Ue_tf32, emb * 4));
+  if (op == kOpNone) CREATE_TRY(cudaMalloc(&c->UT32, (size_t)L * N * (cplx ? 8 : 4)));
+  CREATE_TRY(launch_derive_operands(c, c->stream));
+  CREATE_TRY(cudaMalloc((void**)&c->status, sizeof(int)));
+  CREATE_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+  CREATE_TRY(cudaMallocHost((void**)&c->status_host, sizeof(int)));
+  CREATE_TRY(cudaStreamSynchronize(c->stream));
+#undef CREATE_TRY
+  *out = c;
+  return FFS_OK;
+}
+
+int ffs_create(const double* U, int64_t L, int64_t N, ffs_handle* out) {
+  return ffs_create_ex(U, FFS_F64, L, N, N, 0u, nullptr, out);
+}
+
+int ffs_query(ffs_handle h, int64_t* L, int64_t* N, int* dtype, unsigned* flags, int64_t B,
+              int64_t* bytes_for_B) {
+  if (!h) return fail(nullptr, FFS_E_ARG, "ffs_query: NULL handle");
+  if (L) *L = h->L;
+  if (N) *N = h->N;
+  if (dtype) *dtype = h->dtype;
+  if (flags) *flags = h->flags;
+  if (bytes_for_B) *bytes_for_B = (int64_t)(B * per_sample_bytes(h));
+  return FFS_OK;
+}
+
+int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_index, int64_t n_steps,
+                  int32_t* out_x, int32_t* out_perm, double* out_logp, const int32_t* force_x,
+                  float* out_probs, void* cuda_stream) {
+  if (!h) return fail(nullptr, FFS_E_ARG, "ffs_sample_ex: NULL handle");
+  if (B < 0) return fail(h, FFS_E_ARG, "ffs_sample_ex: B < 0");
+  if (n_steps == 0) n_steps = h->N;
+  if (n_steps < 1 || n_steps > h->N) return fail(h, FFS_E_ARG, "ffs_sample_ex: need 0 <= n_steps <= N");
+  if (B == 0) return FFS_OK;
+  if (!out_x) return fail(h, FFS_E_ARG, "ffs_sample_ex: out_x is NULL");
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : h->stream;
+  const int op = op_mode_of(h->flags);
+  const bool plain = op == kOpNone;
+
+  const bool x_dev = is_device_ptr(out_x);
+  const bool perm_dev = is_device_ptr(out_perm);
+  const bool logp_dev = is_device_ptr(out_logp);
+  const bool force_dev = is_device_ptr(force_x);
+  const bool probs_dev = is_device_ptr(out_probs);
+  const bool any_host = !x_dev || (out_perm && !perm_dev) || (out_logp && !logp_dev) ||
+                        (out_probs && !probs_dev);
+
+  // Wave size from free device memory.
+  size_t per = per_sample_bytes(h);
+  if (!x_dev) per += n_steps * 4;
+  if (force_x && !force_dev) per += n_steps * 4;
+  if (out_probs && !probs_dev) per += (size_t)n_steps * h->L * 4;
+  size_t free_b = 0, total_b = 0;
+  FFS_CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
+  const size_t reserve = (size_t)512 << 20;
+  size_t have = free_b > reserve ? free_b - reserve : 0;
+  have += (size_t)h->ws_B * per_sample_bytes(h);  // the workspace we already hold is reusable
+  int64_t Bw = (int64_t)(have / per);
+  if (Bw < 1) return fail(h, FFS_E_NOMEM, "ffs_sample_ex: not enough device memory for one sample");
+  if (Bw > B) Bw = B;
+  if (Bw > h->ws_B) {
+    int r = ensure_workspace(h, Bw);
+    if (r != FFS_OK) return r;
+  }
+  int32_t* xbuf = nullptr;
+  int32_t* fbuf = nullptr;
+  float* pbuf = nullptr;
+  if (!x_dev) FFS_CUDA_TRY(h, cudaMallocAsync((void**)&xbuf, (size_t)Bw * n_steps * 4, st));
+  if (force_x && !force_dev) FFS_CUDA_TRY(h, cudaMallocAsync((void**)&fbuf, (size_t)Bw * n_steps * 4, st));
+  if (out_probs && !probs_dev)
+    FFS_CUDA_TRY(h, cudaMallocAsync((void**)&pbuf, (size_t)Bw * n_steps * h->L * 4, st));
+
+  int rc = FFS_OK;
+  for (int64_t b0 = 0; b0 < B && rc == FFS_OK; b0 += Bw) {
+    const int64_t bw = (B - b0 < Bw) ? B - b0 : Bw;
+    StepArgs a{};
+    a.L = h->L;
+    a.N = h->N;
+    a.Lr = h->Lr;
+    a.Kr = h->Kr;
+    a.Kp = h->Kp;
+    a.ldP = h->ldP;
+    a.ldMask = h->ldMask;
+    a.bw = bw;
+    a.n_steps = n_steps;
+    a.seed = seed;
+    a.first = first_sample_index + (uint64_t)b0;
+    a.cplx = h->cplx;
+    a.U64 = h->U64;
+    a.m = h->m;
+    a.mask = h->mask;
+    a.H = h->H;
+    a.hplane = h->ws_B * h->Kp;
+    a.P = h->P;
+    a.W = h->W;
+    a.logp = h->logp;
+    a.x = x_dev ? out_x + b0 * n_steps : xbuf;
+    a.probs = out_probs ? (probs_dev ? out_probs + (size_t)b0 * n_steps * h->L : pbuf) : nullptr;
+    a.status = h->status;
+    if (force_x) {
+      if (force_dev) {
+        a.force_x = force_x + b0 * n_steps;
+      } else {
+        FFS_CUDA_TRY(h, cudaMemcpyAsync(fbuf, force_x + b0 * n_steps, (size_t)bw * n_steps * 4,
+                                        cudaMemcpyHostToDevice, st));
+        a.force_x = fbuf;
+      }
+    }
+    if (!plain) FFS_CUDA_TRY(h, cudaMemsetAsync(h->H, 0, (size_t)h->ws_B * h->Kp * op_elem_bytes(op), st));
+    FFS_CUDA_TRY(h, cudaMemsetAsync(h->mask, 0, (size_t)bw * h->ldMask * 4, st));
+    FFS_CUDA_TRY(h, cudaMemsetAsync(h->logp, 0, (size_t)bw * 8, st));
+    TIMED(h, FFS_PHASE_PERM, st, launch_perm_init(a, op, st));
+    for (int64_t k = 0; k < n_steps; ++k) {
+      if (plain)
+        TIMED(h, FFS_PHASE_RESIDUAL, st, launch_residual_plain(a, h->UT32, k, st));
+      else if (op == kOpF32)
+        TIMED(h, FFS_PHASE_RESIDUAL, st, launch_residual_fp32(a, h->Ue32, st));
+      else
+        TIMED(h, FFS_PHASE_RESIDUAL, st, launch_residual_tc(h, a, op, st));
+      TIMED(h, FFS_PHASE_TAIL, st, launch_tail(a, k, state_fp64(h), op, st));
+    }
+    if (!x_dev)
+      FFS_CUDA_TRY(h, cudaMemcpyAsync(out_x + b0 * n_steps, xbuf, (size_t)bw * n_steps * 4,
+                                      cudaMemcpyDeviceToHost, st));
+    if (out_perm)
+      FFS_CUDA_TRY(h, cudaMemcpyAsync(out_perm + b0 * h->N, h->m, (size_t)bw * h->N * 4, cudaMemcpyDefault, st));
+    if (out_logp)
+      FFS_CUDA_TRY(h, cudaMemcpyAsync(out_logp + b0, h->logp, (size_t)bw * 8, cudaMemcpyDefault, st));
+    if (out_probs && !probs_dev)
+      FFS_CUDA_TRY(h, cudaMemcpyAsync(out_probs + (size_t)b0 * n_steps * h->L, pbuf,
+                                      (size_t)bw * n_steps * h->L * 4, cudaMemcpyDeviceToHost, st));
+    if (any_host) FFS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  }
+  if (xbuf) cudaFreeAsync(xbuf, st);
+  if (fbuf) cudaFreeAsync(fbuf, st);
+  if (pbuf) cudaFreeAsync(pbuf, st);
+  if (any_host) {
+    FFS_CUDA_TRY(h, cudaStreamSynchronize(st));
+    FFS_CUDA_TRY(h, cudaMemcpy(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (*h->status_host != 0) {
+      const int code = *h->status_host;
+      cudaMemset(h->status, 0, sizeof(int));
+      return fail(h, code, "ffs_sample_ex: device reported an error (see ffs.h status codes)");
+    }
+  }
+  return rc;
+}
+
+int ffs_sample(ffs_handle h, int64_t B, uint64_t seed, int32_t* out_x) {
+  return ffs_sample_ex(h, B, seed, 0, 0, out_x, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+int ffs_sync(ffs_handle h) {
+  if (!h) return fail(nullptr, FFS_E_ARG, "ffs_sync: NULL handle");
+  FFS_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  FFS_CUDA_TRY(h, cudaMemcpy(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+  const int code = *h->status_host;
+  if (code != 0) {
+    cudaMemset(h->status, 0, sizeof(int));
+    return fail(h, code, "device reported an error (see ffs.h status codes)");
+  }
+  return FFS_OK;
+}
+
+void ffs_destroy(ffs_handle h) { release(h); }
+
+int ffs_profile(ffs_handle h, int enable) {
+  if (!h) return fail(nullptr, FFS_E_ARG, "ffs_profile: NULL handle");
+  if (h->prof) prof_fold(h);
+  h->prof = enable != 0;
+  for (int p = 0; p < 8; ++p) {
+    h->prof_ms[p] = 0.0;
+    h->prof_launches[p] = 0;
+  }
+  return FFS_OK;
+}
+
+int ffs_profile_read(ffs_handle h, double* ms, int64_t* launches, int n) {
+  if (!h) return fail(nullptr, FFS_E_ARG, "ffs_profile_read: NULL handle");
+  if (n < 0 || n > FFS_NUM_PHASES) return fail(h, FFS_E_ARG, "ffs_profile_read: bad n");
+  prof_fold(h);
+  for (int p = 0; p < n; ++p) {
+    if (ms) ms[p] = h->prof_ms[p];
+    if (launches) launches[p] = h->prof_launches[p];
+  }
+  return FFS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Launchers of the libffs kernels (host side).  All launches are asynchronous on the
+// given stream; they check their own launch errors and return cudaError_t.
+#pragma once
+
+#include "ffs_internal.cuh"
+
+namespace fermi {
+
+// Operand encodings of the batched residual (what the per-sample state writes for h).
+enum OpMode : int {
+  kOpNone = 0,    // plain form: no shared operand, the residual reads h from the state
+  kOpF32 = 1,     // FP32, for the CUDA-core residual
+  kOpBF16x3 = 2,  // BF16 hi and lo planes (hi*hi + hi*lo + lo*hi)
+  kOpBF16 = 3,    // BF16 hi plane only
+  kOpTF32 = 4     // FP32 container, rounded to TF32
+};
+
+struct StepArgs {
+  int64_t L, N, Lr, Kr, Kp, ldP, ldMask;
+  int64_t bw;              // samples in this wave
+  int64_t n_steps;
+  uint64_t seed, first;    // Philox key; global index of the wave's first sample
+  bool cplx;
+  const void* U64;         // L x N (double / cd)
+  const int32_t* m;        // bw x N
+  uint32_t* mask;          // bw x ldMask
+  void* H;                 // bw x Kp operand planes
+  int64_t hplane;          // elements per operand plane (capacity x Kp)
+  float* P;                // bw x ldP
+  void* W;                 // bw x N x N state
+  double* logp;            // bw
+  int32_t* x;              // bw x n_steps
+  const int32_t* force_x;  // bw x n_steps or null
+  float* probs;            // bw x n_steps x L or null
+  int* status;
+};
+
+cudaError_t launch_perm_init(const StepArgs& a, int op_mode, cudaStream_t s);
+cudaError_t launch_ortho_check(const void* U64, bool cplx, int64_t L, int64_t N, double* maxdev,
+                               cudaStream_t s);
+cudaError_t launch_derive_operands(ffs_ctx* c, cudaStream_t s);
+cudaError_t launch_residual_fp32(const StepArgs& a, const float* Ue32, cudaStream_t s);
+cudaError_t launch_residual_plain(const StepArgs& a, const void* UT32, int64_t k, cudaStream_t s);
+// state_fp64: FP64 (double / cd) state, else FP32 (float / cf).
+cudaError_t launch_tail(const StepArgs& a, int64_t k, bool state_fp64, int op_mode, cudaStream_t s);
+size_t tail_smem_bytes(int64_t N, bool cplx, bool state_fp64);
+cudaError_t configure_kernels(int64_t N, bool cplx);
+
+}  // namespace fermi

@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (absolute, on normalised conditional probabilities, teacher-forced on the
+oracle's prefix and column order so one divergent draw cannot cascade):
+  FP32 residual with FP64 state, and the plain per-sample FP32 form:   1e-6
+  BF16x3 tensor-core residual (the batched mixed-precision form):      1e-4
+  TF32 / BF16 single-product residuals (no accuracy target; bounds):   2e-3 / 2e-2
+Free-running draws must be identical to the oracle's except where the uniform lies
+within eps of an oracle CDF boundary between the two sites (eps = the mode's
+probability tolerance).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import ffs_oracle as o
+from paper_2109_07358_gb300 import ffs
+from paper_2109_07358_gb300 import workloads as w
+from tests.parity_util import draw_identity, oracle_runs, oracle_runs_parallel
+
+pytestmark = pytest.mark.gpu
+
+MODES = {
+    "fp32": (ffs.FFS_RES_FP32 | ffs.FFS_STATE_FP64, 1e-6),
+    "plain": (ffs.FFS_FORM_PLAIN, 1e-6),
+    "bf16x3": (ffs.FFS_RES_BF16X3 | ffs.FFS_STATE_FP64, 1e-4),
+    "tf32": (ffs.FFS_RES_TF32 | ffs.FFS_STATE_FP64, 2e-3),
+    "bf16": (ffs.FFS_RES_BF16 | ffs.FFS_STATE_FP64, 2e-2),
+}
+
+CASES = {
+    "real": lambda: w.haar(300, 40, seed=1, complex_=False),
+    "complex": lambda: w.haar(200, 30, seed=2),
+    "lattice": lambda: w.square_lattice(8, 8, 16, seed=0),
+}
+B = 70      # two 64-sample tiles and a ragged tail
+SEED = 12345
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2109_07358_gb300.build import build
+
+    build()
+    assert torch.cuda.is_available()
+
+
+_U = {}
+_R = {}
+
+
+def U_of(case):
+    if case not in _U:
+        _U[case] = CASES[case]()
+    return _U[case]
+
+
+def recs_of(case):
+    if case not in _R:
+        _R[case] = oracle_runs(U_of(case), SEED, range(B))
+    return _R[case]
+
+
+def sampler(U, flags):
+    return ffs.Sampler(torch.from_numpy(np.ascontiguousarray(U)).cuda(), flags)
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 64, 257])
+def test_permutations_bit_exact(N):
+    U = w.haar(max(N, 8), N, seed=N)
+    S = sampler(U, ffs.FFS_RES_FP32)
+    out = S.sample(33, seed=2**40 + 5, first_sample_index=2**33 - 7, perm=True)
+    S.sync()
+    P = out["perm"].cpu().numpy()
+    for b in range(33):
+        assert np.array_equal(P[b], o.permutation(2**40 + 5, 2**33 - 7 + b, N))
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("case", list(CASES))
+def test_teacher_forced_conditionals(case, mode):
+    flags, tol = MODES[mode]
+    U = U_of(case)
+    recs = recs_of(case)
+    L, N = U.shape
+    S = sampler(U, flags)
+    force = torch.tensor(np.stack([r["x"] for r in recs]), dtype=torch.int32, device="cuda")
+    out = S.sample(B, SEED, force_x=force, probs=True, perm=True, logp=True)
+    S.sync()
+    probs = out["probs"].cpu().double().numpy()
+    ref = np.stack([r["probs"] for r in recs])
+    err = float(np.abs(probs - ref).max())
+    print(f"{case} {mode}: max |dP| = {err:.3e} (tol {tol:.0e})")
+    assert err <= tol
+    assert np.array_equal(out["x"].cpu().numpy(), force.cpu().numpy())
+    assert np.array_equal(out["perm"].cpu().numpy(), np.stack([r["m"] for r in recs]))
+    lp = out["logp"].cpu().numpy()
+    ref_lp = np.array([r["logp"] for r in recs])
+    assert np.all(np.abs(lp - ref_lp) <= 1e-3 * np.maximum(1.0, np.abs(ref_lp)))
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("case", list(CASES))
+def test_free_running_draws_match(case, mode):
+    flags, tol = MODES[mode]
+    U = U_of(case)
+    recs = recs_of(case)
+    S = sampler(U, flags)
+    X = S.sample(B, SEED)["x"].cpu().numpy()
+    S.sync()
+    frac, bad = draw_identity(X, recs, eps=max(tol, 1e-6))
+    print(f"{case} {mode}: identical {frac:.4f}, unexcused {bad}")
+    assert not bad
+    assert frac >= 0.95
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16x3", "plain"])
+def test_chain_L64_N8_full_batch(mode):
+    """The small plain workload: open chain L = 64, N = 8, 10^4 samples, seed 0."""
+    flags, tol = MODES[mode]
+    U = w.chain_L64_N8()
+    n = 10_000
+    recs = oracle_runs_parallel(U, 0, 0, n)
+    S = sampler(U, flags)
+    X = S.sample(n, 0)["x"].cpu().numpy()
+    S.sync()
+    frac, bad = draw_identity(X, recs, eps=max(tol, 1e-6))
+    print(f"chain64 {mode}: identical {frac:.5f}, unexcused {len(bad)}")
+    assert not bad
+    assert frac >= 0.999
+
+
+def test_brute_force_chi2_on_gpu_samples():
+    from scipy import stats
+
+    U = w.open_chain(12, 4)
+    P = o.set_probabilities(U)
+    n = 10_000
+    S = sampler(U, ffs.FFS_RES_BF16X3)
+    X = S.sample(n, 0)["x"].cpu().numpy()
+    counts = {}
+    for x in X:
+        key = tuple(sorted(x.tolist()))
+        counts[key] = counts.get(key, 0) + 1
+    keys = sorted(P, key=lambda s: P[s])
+    obs, exp, ao, ae = [], [], 0.0, 0.0
+    for s in keys:
+        ao += counts.get(s, 0)
+        ae += P[s] * n
+        if ae >= 5:
+            obs.append(ao)
+            exp.append(ae)
+            ao = ae = 0.0
+    obs[-1] += ao
+    exp[-1] += ae
+    assert stats.chisquare(obs, np.array(exp) * n / np.sum(exp)).pvalue > 0.01
+
+
+def test_marginal_prefix_and_sharding_invariance():
+    U = w.haar(256, 48, seed=7)
+    S = sampler(U, ffs.FFS_RES_BF16X3)
+    full = S.sample(100, 3)["x"].cpu().numpy()
+    part = S.sample(100, 3, n_steps=17)["x"].cpu().numpy()
+    assert np.array_equal(full[:, :17], part)
+    a = S.sample(37, 3)["x"].cpu().numpy()
+    b = S.sample(63, 3, first_sample_index=37)["x"].cpu().numpy()
+    assert np.array_equal(np.concatenate([a, b]), full)
+
+
+def test_host_buffers_equal_device_buffers():
+    U = w.haar(150, 20, seed=8)
+    S = sampler(U, ffs.FFS_RES_BF16X3)
+    dev = S.sample(40, 9)["x"].cpu()
+    host = torch.empty((40, 20), dtype=torch.int32)
+    ffs.ffs_sample(S.h, 40, 9, host)
+    assert torch.equal(dev, host)
+    pinned = torch.empty((40, 20), dtype=torch.int32).pin_memory()
+    ffs.ffs_sample(S.h, 40, 9, pinned)
+    assert torch.equal(dev, pinned)
+
+
+def test_edge_sizes():
+    # N = 1: the conditional is the Born rule |U_y1|^2
+    U = w.haar(50, 1, seed=3)
+    S = sampler(U, ffs.FFS_RES_FP32)
+    out = S.sample(5, 0, probs=True)
+    assert np.allclose(out["probs"].cpu().numpy()[:, 0], np.abs(U[:, 0]) ** 2, atol=1e-6)
+    # N = L: every sample is a permutation of all sites
+    U = w.haar(33, 33, seed=4)
+    S = sampler(U, ffs.FFS_RES_BF16X3)
+    X = S.sample(20, 1)["x"].cpu().numpy()
+    assert all(sorted(x.tolist()) == list(range(33)) for x in X)
+    # B = 0 is a no-op
+    ffs.ffs_sample(S.h, 0, 0, None)
+
+
+def test_errors_are_reported():
+    U = w.haar(40, 5, seed=5)
+    bad = U.copy()
+    bad[:, 0] *= 1.01
+    with pytest.raises(ffs.FFSError) as e:
+        sampler(bad, 0)
+    assert e.value.code == ffs.FFS_E_NOT_ORTHONORMAL
+    with pytest.raises(ffs.FFSError) as e:
+        ffs.ffs_create(torch.from_numpy(U[:4]).cuda(), 4, 5)
+    assert e.value.code == ffs.FFS_E_ARG
+    with pytest.raises(ffs.FFSError) as e:
+        ffs.ffs_create_ex(torch.from_numpy(U).cuda(), ffs.FFS_F64, 40, 5, 5, 0x8000)
+    assert e.value.code == ffs.FFS_E_ARG
+    S = sampler(U, ffs.FFS_RES_FP32)
+    force = torch.full((3, 5), 999, dtype=torch.int32, device="cuda")
+    S.sample(3, 0, force_x=force)
+    with pytest.raises(ffs.FFSError) as e:
+        S.sync()
+    assert e.value.code == ffs.FFS_E_ARG
+    S.sync()  # the status word was cleared
