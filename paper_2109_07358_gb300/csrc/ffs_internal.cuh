@@ -5,6 +5,7 @@
 // using the normal vector h of Eq. 3.  Internally everything is 0-based.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -171,6 +172,12 @@ struct ffs_ctx {
   int64_t probs_cap = 0;
   int64_t ldP = 0;
   int64_t ldMask = 0;
+
+  // TMA descriptors of the tensor-core residual: the two planes of Ue and of H.
+  CUtensorMap tmU[2];
+  CUtensorMap tmH[2];
+  int tm_U_ready = -1;   // operand mode tmU was encoded for
+  int64_t tm_H_B = -1;   // workspace capacity tmH was encoded for
   int* status = nullptr;         // device status word
   int* status_host = nullptr;    // pinned mirror
 

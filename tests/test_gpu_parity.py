@@ -7,7 +7,8 @@ oracle's prefix and column order so one divergent draw cannot cascade):
   TF32 / BF16 single-product residuals (no accuracy target; bounds):   2e-3 / 2e-2
 Free-running draws must be identical to the oracle's except where the uniform lies
 within eps of an oracle CDF boundary between the two sites (eps = the mode's
-probability tolerance).
+probability tolerance); for the modes with an accuracy target at least 99.9% of the
+10^4 chain samples (95% of the 70-sample cases) must be identical.
 """
 import math
 
@@ -113,7 +114,8 @@ def test_free_running_draws_match(case, mode):
     frac, bad = draw_identity(X, recs, eps=max(tol, 1e-6))
     print(f"{case} {mode}: identical {frac:.4f}, unexcused {bad}")
     assert not bad
-    assert frac >= 0.95
+    if mode in ("fp32", "plain", "bf16x3"):   # the modes with an accuracy target
+        assert frac >= 0.95
 
 
 @pytest.mark.parametrize("mode", ["fp32", "bf16x3", "plain"])
