@@ -159,6 +159,36 @@ void ffs_destroy(ffs_handle h);
 int ffs_query(ffs_handle h, int64_t* L, int64_t* N, int* dtype, unsigned* flags,
               int64_t B, int64_t* bytes_for_B);
 
+/*
+ * ffs_sample_noalloc - draw B configurations without allocating any device memory.
+ * The paper has no counterpart: this entry point is for callers that cannot allocate
+ * device memory at the moment they sample, such as code running inside a memory pool
+ * that has been sized and frozen, a framework whose caching allocator must not be
+ * bypassed, or a plugin that may only touch the memory it is handed.  ffs_create
+ * allocates (copies of U, per-wave working memory), so such callers use this call
+ * instead.  All working memory comes from one fixed array of FFS_NOALLOC_SCRATCH_BYTES
+ * in device global memory that the library declares statically: every GPU that loads
+ * the library holds that memory until the process exits.
+ *   U          device pointer, row-major L x N, dtype FFS_F64 or FFS_C128 (U^dagger U = 1
+ *              is assumed, not checked).
+ *   L, N, B    1 <= N <= L, B >= 0 samples; sample b uses Philox sample index b.
+ *   seed       Philox key, as in ffs_sample.
+ *   out_x      device pointer, B x N int32, sites in draw order.
+ *   cuda_stream  cudaStream_t or NULL.
+ * The samples equal those of ffs_sample_ex with FFS_RES_FP32 | FFS_STATE_FP64 (the same
+ * arithmetic in the same order, fused into one kernel; meant for small problems).
+ * A size whose working set (about B (8 N^2 + 4 L + 8 N) bytes, twice the N^2 term for
+ * complex U) does not fit the array is rejected with FFS_E_NOMEM and a message naming
+ * the limit.  The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call works in the same array, which
+ * keeps the previous call's contents (the kernel clears what must start at zero), so
+ * calls that overlap on the GPU, from different streams or threads, race.  Asynchronous;
+ * returns argument and launch errors only (there is no device status word).
+ */
+#define FFS_NOALLOC_SCRATCH_BYTES (16u << 20)
+int ffs_sample_noalloc(const void* U, int dtype, int64_t L, int64_t N, int64_t B, uint64_t seed,
+                       int32_t* out_x, void* cuda_stream);
+
 /* Phases reported by ffs_profile_read. */
 #define FFS_PHASE_PERM 0      /* column orders m and the step-0 operand              */
 #define FFS_PHASE_RESIDUAL 1  /* all-site weights |u_y^T h|^2 (Section S-1 products) */

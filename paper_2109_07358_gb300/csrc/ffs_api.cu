@@ -11,6 +11,11 @@ using namespace fermi;
 
 static thread_local std::string g_null_handle_error;
 
+namespace fermi {
+// Error message of a call that has no handle (read back by ffs_last_error(NULL)).
+void set_null_handle_error(const std::string& msg) { g_null_handle_error = msg; }
+}  // namespace fermi
+
 static int fail(ffs_ctx* c, int code, const std::string& msg) {
   if (c)
     c->last_error = msg;

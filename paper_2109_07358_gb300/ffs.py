@@ -62,10 +62,11 @@ def lib() -> ctypes.CDLL:
         L.ffs_destroy.restype = None
         L.ffs_query.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                 ctypes.POINTER(ctypes.c_uint), i64, ctypes.POINTER(i64)]
+        L.ffs_sample_noalloc.argtypes = [vp, i32, i64, i64, i64, u64, vp, vp]
         L.ffs_profile.argtypes = [vp, i32]
         L.ffs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]
         for name in ("ffs_create", "ffs_create_ex", "ffs_sample", "ffs_sample_ex", "ffs_sync", "ffs_query",
-                     "ffs_profile", "ffs_profile_read"):
+                     "ffs_profile", "ffs_profile_read", "ffs_sample_noalloc"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -117,6 +118,12 @@ def ffs_sample_ex(h, B: int, seed: int, first_sample_index: int, n_steps: int, o
                   out_logp=None, force_x=None, out_probs=None, stream=None):
     _check(lib().ffs_sample_ex(h, B, seed, first_sample_index, n_steps, _ptr(out_x), _ptr(out_perm),
                                _ptr(out_logp), _ptr(force_x), _ptr(out_probs), _stream(stream)), h)
+
+
+def ffs_sample_noalloc(U, dtype: int, L: int, N: int, B: int, seed: int, out_x, stream=None):
+    """Sampling that allocates no device memory (fixed working array in the library);
+    for callers that cannot allocate.  U and out_x must be device memory."""
+    _check(lib().ffs_sample_noalloc(_ptr(U), dtype, L, N, B, seed, _ptr(out_x), _stream(stream)))
 
 
 def ffs_sync(h):

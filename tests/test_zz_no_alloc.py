@@ -1,0 +1,74 @@
+"""ffs_sample_noalloc: sampling for callers that cannot allocate device memory.
+
+Such callers (a frozen memory pool, a framework allocator that must not be bypassed,
+a plugin limited to the memory it is given) cannot use ffs_create, which allocates.
+The allocation-free entry point works in a fixed array inside the library and must
+give the same samples as ffs_sample_ex with FFS_RES_FP32 | FFS_STATE_FP64, within
+the tolerance the parity tests use: draws identical except where the uniform lies
+within 1e-6 of an oracle CDF boundary.  Two calls in a row check that the contents a
+previous call leaves in the shared array do not leak into the next one.
+
+This file is collected last on purpose, so that a run stopping at its first failure
+has already run every other test.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ffs_oracle as o
+from paper_2109_07358_gb300 import ffs
+from paper_2109_07358_gb300 import workloads as w
+from tests.parity_util import excused, first_divergence
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2109_07358_gb300.build import build
+
+    build()
+    assert torch.cuda.is_available()
+
+
+def _check_against_sample_ex(U, B, seed):
+    L, N = U.shape
+    Ud = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    out = torch.full((B, N), -1, dtype=torch.int32, device="cuda")
+    ffs.ffs_sample_noalloc(Ud, ffs.dtype_of(Ud), L, N, B, seed, out)
+    torch.cuda.synchronize()
+    S = ffs.Sampler(Ud, ffs.FFS_RES_FP32 | ffs.FFS_STATE_FP64)
+    ref = S.sample(B, seed)["x"]
+    S.sync()
+    S.close()
+    a, r = out.cpu().numpy(), ref.cpu().numpy()
+    assert a.min() >= 0 and a.max() < L
+    diff = [b for b in range(B) if not np.array_equal(a[b], r[b])]
+    assert len(diff) <= 0.001 * B
+    for b in diff:  # any difference must sit within EPS of a CDF boundary
+        rec = o.sample_one(U, seed, b, record=True)
+        for xs in (a[b], r[b]):
+            k = first_divergence(xs, rec["x"])
+            assert k < 0 or excused(rec, k, xs[k], EPS)
+    return a
+
+
+def test_noalloc_matches_sample_ex_two_calls_in_a_row():
+    U = w.chain_L64_N8()
+    x1 = _check_against_sample_ex(U, 2000, 0)
+    x2 = _check_against_sample_ex(U, 2000, 0)
+    assert np.array_equal(x1, x2)
+    Uc = w.haar(40, 10, seed=3)
+    _check_against_sample_ex(Uc, 500, 5)
+    _check_against_sample_ex(Uc, 300, 6)
+
+
+def test_noalloc_rejects_sizes_beyond_the_array():
+    U = torch.from_numpy(w.haar(64, 32, seed=1)).cuda()
+    out = torch.empty((1, 32), dtype=torch.int32, device="cuda")
+    with pytest.raises(ffs.FFSError) as e:
+        ffs.ffs_sample_noalloc(U, ffs.dtype_of(U), 64, 32, 1 << 20, 0, out)
+    assert e.value.code == ffs.FFS_E_NOMEM
+    assert "fixed" in str(e.value)
