@@ -146,6 +146,23 @@ def oracle_baseline(U, n_samples, seed=0, workers=None):
     workers = max(1, min(workers or os.cpu_count() or 1, n_samples))
     bounds = np.linspace(0, n_samples, workers + 1).astype(int)
     jobs = [(U, seed, int(bounds[i]), int(bounds[i + 1])) for i in range(workers)]
+    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in saved:  # children start with single-threaded BLAS (read at their numpy import)
+        os.environ[v] = "1"
+    try:
+        return _oracle_pool(jobs, workers, n_samples)
+    finally:
+        for v, old in saved.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+
+
+def _oracle_pool(jobs, workers, n_samples):
+    import multiprocessing as mp
+
+    U = jobs[0][0]
     with mp.get_context("spawn").Pool(workers) as pool:
         pool.map(_oracle_worker, [(U[:8, :2].copy() / np.linalg.norm(U[:8, :2], axis=0), 0, 0, 1)] * workers)
         t0 = time.perf_counter()
@@ -194,6 +211,7 @@ def main():
     ap.add_argument("--workload", default="lattice64x64_N1024_B4096", choices=list(WORKLOADS))
     ap.add_argument("--B", type=int, default=0, help="override samples per step")
     ap.add_argument("--chosen", default="bf16x3", choices=["bf16x3", "fp32", "tf32", "bf16"])
+    ap.add_argument("--state", default="df64", choices=["df64", "fp64", "fp32"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -235,7 +253,8 @@ def main():
     U = torch.from_numpy(U_np).cuda()
     res_flag = {"bf16x3": ffs.FFS_RES_BF16X3, "fp32": ffs.FFS_RES_FP32, "tf32": ffs.FFS_RES_TF32,
                 "bf16": ffs.FFS_RES_BF16}[args.chosen]
-    flags = res_flag | ffs.FFS_STATE_FP64
+    state_flag = {"df64": ffs.FFS_STATE_DF64, "fp64": ffs.FFS_STATE_FP64, "fp32": ffs.FFS_STATE_FP32}[args.state]
+    flags = res_flag | state_flag
     stream = torch.cuda.Stream()
     S = ffs.Sampler(U, flags, stream=stream)
     x = torch.empty((B, N), dtype=torch.int32, device="cuda")
@@ -272,6 +291,7 @@ def main():
     # per-phase roofline
     res_ms, res_n = prof["residual"]
     tail_ms, tail_n = prof["tail"]
+    panel_ms, panel_n = prof["panel"]
     perm_ms, perm_n = prof["perm"]
     res_flops = flops_per_sample(L, N, cplx) * B * args.steps
     issued = 2 * (2 * L) * (2 * N) * N * B * args.steps if cplx else 2 * L * N * N * B * args.steps
@@ -287,16 +307,23 @@ def main():
         "residual": {"ms": res_ms / args.steps, "launches_per_step": res_n / args.steps,
                      "algorithmic_tflops": res_flops / (res_ms / 1e3) / 1e12 if res_ms else None,
                      "issued_tflops": issued * mult / (res_ms / 1e3) / 1e12 if res_ms else None},
-        "tail": {"ms": tail_ms / args.steps, "launches_per_step": tail_n / args.steps,
-                 "fp64_tflops": tail_fl / (tail_ms / 1e3) / 1e12 if tail_ms else None},
+        "tail_step": {"ms": tail_ms / args.steps, "launches_per_step": tail_n / args.steps},
+        "tail_panel": {"ms": panel_ms / args.steps, "launches_per_step": panel_n / args.steps},
+        "tail_total": {"ms": (tail_ms + panel_ms) / args.steps,
+                       "state_tflops": tail_fl / ((tail_ms + panel_ms) / 1e3) / 1e12 if tail_ms else None},
         "perm": {"ms": perm_ms / args.steps, "launches_per_step": perm_n / args.steps},
     }
-    dominant = "tail" if tail_ms >= res_ms else "residual"
+    tail_all = tail_ms + panel_ms
+    dominant = "tail" if tail_all >= res_ms else "residual"
     if dominant == "tail":
-        ach = tail_fl / (tail_ms / 1e3) / 1e12
-        roof = {"kernel": "tail (draw + FP64 state update)", "bound": "alu", "achieved": ach,
-                "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s", "frac": ach / NOMINAL_FP64_TFLOPS,
-                "traffic": None, "peak_source": "nominal FP64 rate (1.25 TFLOP/s)"}
+        ach = tail_fl / (tail_all / 1e3) / 1e12
+        # state flops per FP32-pipe op: 1 (FP32 FMA = 2 flops / 2), double-float about 1/6
+        peak, src = {"fp64": (NOMINAL_FP64_TFLOPS, "nominal FP64 rate (1.25 TFLOP/s)"),
+                     "fp32": (NOMINAL_FP32_TFLOPS, "nominal FP32 rate"),
+                     "df64": (NOMINAL_FP32_TFLOPS / 6, "nominal FP32 rate / 6 (double-float multiply-add "
+                              "= 6 FP32 FMA-equivalents)")}[args.state]
+        roof = {"kernel": f"state update ({args.state}, per-step + per-panel)", "bound": "alu", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_source": src}
     else:
         ach = res_flops / (res_ms / 1e3) / 1e12
         roof = {"kernel": f"residual ({args.chosen})", "bound": res_bound, "achieved": ach, "peak": res_peak,
@@ -304,16 +331,17 @@ def main():
                 "peak_source": f"{peaks['source']} bf16 sustained / {mult}" if res_bound == "tensor"
                 else "nominal FP32 rate"}
 
+    prof_launches = int(res_n + tail_n + panel_n + perm_n) // args.steps
     out = {
         "metric": "FFS samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64" if cplx else "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": spec["desc"], "L": L, "N": N, "B": B,
-                   "form": f"batched {args.chosen} residual + FP64 state", "l2": "inputs larger than L2 "
+                   "form": f"batched {args.chosen} residual + {args.state} state", "l2": "inputs larger than L2 "
                    "(the per-sample state of a batch is tens of GB)"},
         "clocks": clk.summary(),
-        "gpu_launches": int(res_n + tail_n + perm_n) // args.steps,
+        "gpu_launches": prof_launches,
         "roofline": roof,
         "phases": phases,
     }

@@ -70,7 +70,13 @@ typedef enum {
  *   FFS_RES_TF32    tensor cores, one TF32 product, FP32 accumulation
  * Per-sample elimination state (the normal vector h, the pivots):
  *   FFS_STATE_FP64  IEEE double                                 (default)
+ *   FFS_STATE_DF64  double-float: pairs of FP32 numbers, about 48 significant bits,
+ *                   computed on the FP32 pipes (FP64-class precision)
  *   FFS_STATE_FP32  IEEE float (used by the plain form)
+ * State update schedule:
+ *   (default)           blocked: per step the new row is reduced on a 32-column panel,
+ *                       the remaining columns are updated once per panel
+ *   FFS_TAIL_UNBLOCKED  every step updates all remaining columns (FP64 or FP32 state)
  * Form:
  *   FFS_FORM_BATCHED  all samples of a wave share one contraction per step (default)
  *   FFS_FORM_PLAIN    the plain per-sample form: per sample, an FP32 CUDA-core
@@ -85,11 +91,13 @@ typedef enum {
 #define FFS_RES_MASK 0xFu
 #define FFS_STATE_FP64 0x00u
 #define FFS_STATE_FP32 0x10u
+#define FFS_STATE_DF64 0x20u
 #define FFS_STATE_MASK 0xF0u
 #define FFS_FORM_BATCHED 0x000u
 #define FFS_FORM_PLAIN 0x100u
 #define FFS_FORM_MASK 0xF00u
 #define FFS_NO_ORTHO_CHECK 0x1000u
+#define FFS_TAIL_UNBLOCKED 0x2000u
 
 /* Tolerance of the orthonormality check: max_ij |(U^dagger U)_ij - delta_ij|. */
 #define FFS_ORTHO_TOL 1e-6
@@ -175,8 +183,9 @@ int ffs_query(ffs_handle h, int64_t* L, int64_t* N, int* dtype, unsigned* flags,
  *   seed       Philox key, as in ffs_sample.
  *   out_x      device pointer, B x N int32, sites in draw order.
  *   cuda_stream  cudaStream_t or NULL.
- * The samples equal those of ffs_sample_ex with FFS_RES_FP32 | FFS_STATE_FP64 (the same
- * arithmetic in the same order, fused into one kernel; meant for small problems).
+ * The samples equal those of ffs_sample_ex with FFS_RES_FP32 | FFS_STATE_FP64 |
+ * FFS_TAIL_UNBLOCKED (the same arithmetic in the same order, fused into one kernel;
+ * meant for small problems).
  * A size whose working set (about B (8 N^2 + 4 L + 8 N) bytes, twice the N^2 term for
  * complex U) does not fit the array is rejected with FFS_E_NOMEM and a message naming
  * the limit.  The first call on a device looks up the array's device address; make that
@@ -192,8 +201,9 @@ int ffs_sample_noalloc(const void* U, int dtype, int64_t L, int64_t N, int64_t B
 /* Phases reported by ffs_profile_read. */
 #define FFS_PHASE_PERM 0      /* column orders m and the step-0 operand              */
 #define FFS_PHASE_RESIDUAL 1  /* all-site weights |u_y^T h|^2 (Section S-1 products) */
-#define FFS_PHASE_TAIL 2      /* draw, pivot and elimination-state update            */
-#define FFS_NUM_PHASES 3
+#define FFS_PHASE_TAIL 2      /* draw, pivot and per-step elimination-state update   */
+#define FFS_PHASE_PANEL 3     /* once-per-panel update of the remaining state columns */
+#define FFS_NUM_PHASES 4
 
 /*
  * ffs_profile - enable (1) or disable (0) per-phase timing of h: every kernel launch

@@ -67,9 +67,19 @@ static size_t op_elem_bytes(int op) {
 
 static bool state_fp64(const ffs_ctx* c) { return (c->flags & FFS_STATE_MASK) == FFS_STATE_FP64; }
 
-static size_t state_elem_bytes(const ffs_ctx* c) {
-  return (c->cplx ? 2 : 1) * (state_fp64(c) ? sizeof(double) : sizeof(float));
+static int state_kind(const ffs_ctx* c) {
+  switch (c->flags & FFS_STATE_MASK) {
+    case FFS_STATE_FP32: return kStateFP32;
+    case FFS_STATE_DF64: return kStateDF64;
+    default: return kStateFP64;
+  }
 }
+
+static bool blocked(const ffs_ctx* c) {
+  return op_mode_of(c->flags) != kOpNone && !(c->flags & FFS_TAIL_UNBLOCKED);
+}
+
+static size_t state_elem_bytes(const ffs_ctx* c) { return blocked_elem_bytes(c->cplx, state_kind(c)); }
 
 // Device bytes per sample of a wave (not counting optional outputs).
 static size_t per_sample_bytes(const ffs_ctx* c) {
@@ -81,6 +91,10 @@ static size_t per_sample_bytes(const ffs_ctx* c) {
   b += (size_t)c->ldP * 4;                         // weights
   b += (size_t)c->N * c->N * state_elem_bytes(c);  // elimination state
   b += 8;                                          // logp
+  if (blocked(c)) {                                // saved panel vectors, couplings, pivots
+    const size_t nb = blocked_panel_width();
+    b += ((size_t)c->N * nb + nb * nb + nb) * state_elem_bytes(c);
+  }
   return b;
 }
 
@@ -90,7 +104,13 @@ static void free_workspace(ffs_ctx* c) {
   cudaFree(c->H);
   cudaFree(c->P);
   cudaFree(c->W);
+  cudaFree(c->WsT);
+  cudaFree(c->beta);
+  cudaFree(c->piv);
   cudaFree(c->logp);
+  c->WsT = nullptr;
+  c->beta = nullptr;
+  c->piv = nullptr;
   c->m = nullptr;
   c->mask = nullptr;
   c->H = nullptr;
@@ -111,6 +131,12 @@ static int ensure_workspace(ffs_ctx* c, int64_t Bw) {
   FFS_CUDA_TRY(c, cudaMalloc((void**)&c->P, (size_t)Bw * c->ldP * 4));
   FFS_CUDA_TRY(c, cudaMalloc(&c->W, (size_t)Bw * c->N * c->N * state_elem_bytes(c)));
   FFS_CUDA_TRY(c, cudaMalloc((void**)&c->logp, (size_t)Bw * 8));
+  if (blocked(c)) {
+    const size_t nb = blocked_panel_width(), es = state_elem_bytes(c);
+    FFS_CUDA_TRY(c, cudaMalloc(&c->WsT, (size_t)Bw * c->N * nb * es));
+    FFS_CUDA_TRY(c, cudaMalloc(&c->beta, (size_t)Bw * nb * nb * es));
+    FFS_CUDA_TRY(c, cudaMalloc(&c->piv, (size_t)Bw * nb * es));
+  }
   c->ws_B = Bw;
   return FFS_OK;
 }
@@ -205,11 +231,13 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
   if (L > (int64_t)1 << 30) return fail(nullptr, FFS_E_ARG, "ffs_create_ex: L too large");
   const bool cplx = (dtype == FFS_C128 || dtype == FFS_C64);
   if ((flags & FFS_FORM_MASK) == FFS_FORM_PLAIN)
-    flags = (flags & ~(FFS_RES_MASK | FFS_STATE_MASK)) | FFS_RES_FP32 | FFS_STATE_FP32;
-  if ((flags & FFS_FORM_MASK) > FFS_FORM_PLAIN || (flags & FFS_STATE_MASK) > FFS_STATE_FP32 ||
-      (flags & ~(FFS_RES_MASK | FFS_STATE_MASK | FFS_FORM_MASK | FFS_NO_ORTHO_CHECK)) ||
+    flags = (flags & ~(FFS_RES_MASK | FFS_STATE_MASK)) | FFS_RES_FP32 | FFS_STATE_FP32 | FFS_TAIL_UNBLOCKED;
+  if ((flags & FFS_FORM_MASK) > FFS_FORM_PLAIN || (flags & FFS_STATE_MASK) > FFS_STATE_DF64 ||
+      (flags & ~(FFS_RES_MASK | FFS_STATE_MASK | FFS_FORM_MASK | FFS_NO_ORTHO_CHECK | FFS_TAIL_UNBLOCKED)) ||
       op_mode_of(flags) < 0)
     return fail(nullptr, FFS_E_ARG, "ffs_create_ex: bad flags");
+  if ((flags & FFS_TAIL_UNBLOCKED) && (flags & FFS_STATE_MASK) == FFS_STATE_DF64)
+    return fail(nullptr, FFS_E_ARG, "ffs_create_ex: the unblocked state update has no double-float form");
 
   ffs_ctx* c = new ffs_ctx();
   c->L = L;
@@ -218,7 +246,8 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
   c->cplx = cplx;
   c->flags = flags;
   c->stream = (cudaStream_t)cuda_stream;
-  const size_t smem_need = tail_smem_bytes(N, cplx, state_fp64(c));
+  const size_t smem_need = blocked(c) ? blocked_step_smem(N, cplx, state_kind(c))
+                                     : tail_smem_bytes(N, cplx, state_fp64(c));
   if (smem_need > 224 * 1024) {
     int r = fail(nullptr, FFS_E_UNSUPPORTED, "ffs_create_ex: N too large for the per-sample state kernel");
     release(c);
@@ -240,6 +269,7 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
   if (!configured) {
     CREATE_TRY(configure_kernels(N, cplx));
     CREATE_TRY(configure_residual_tc());
+    CREATE_TRY(configure_blocked());
     configured = true;
   }
   c->Lr = cplx ? 2 * L : L;
@@ -394,6 +424,12 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
         a.force_x = fbuf;
       }
     }
+    BlockedArgs bt{};
+    bt.Nc = n_steps;
+    bt.W = h->W;
+    bt.WsT = h->WsT;
+    bt.beta = h->beta;
+    bt.piv = h->piv;
     if (!plain) FFS_CUDA_TRY(h, cudaMemsetAsync(h->H, 0, (size_t)h->ws_B * h->Kp * op_elem_bytes(op), st));
     FFS_CUDA_TRY(h, cudaMemsetAsync(h->mask, 0, (size_t)bw * h->ldMask * 4, st));
     FFS_CUDA_TRY(h, cudaMemsetAsync(h->logp, 0, (size_t)bw * 8, st));
@@ -405,7 +441,15 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
         TIMED(h, FFS_PHASE_RESIDUAL, st, launch_residual_fp32(a, h->Ue32, st));
       else
         TIMED(h, FFS_PHASE_RESIDUAL, st, launch_residual_tc(h, a, op, st));
-      TIMED(h, FFS_PHASE_TAIL, st, launch_tail(a, k, state_fp64(h), op, st));
+      if (blocked(h)) {
+        TIMED(h, FFS_PHASE_TAIL, st, launch_blocked_step(a, bt, k, state_kind(h), op, st));
+        const int64_t nb = blocked_panel_width();
+        const int64_t k0 = (k / nb) * nb, k1 = (k0 + nb < n_steps) ? k0 + nb : n_steps;
+        if (k + 1 == k1 && k1 < n_steps)
+          TIMED(h, FFS_PHASE_PANEL, st, launch_blocked_panel(a, bt, k0, k1, state_kind(h), op, st));
+      } else {
+        TIMED(h, FFS_PHASE_TAIL, st, launch_tail(a, k, state_fp64(h), op, st));
+      }
     }
     if (!x_dev)
       FFS_CUDA_TRY(h, cudaMemcpyAsync(out_x + b0 * n_steps, xbuf, (size_t)bw * n_steps * 4,

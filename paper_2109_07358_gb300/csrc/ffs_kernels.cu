@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <type_traits>
 
+#include "ffs_draw.cuh"
 #include "ffs_kernels.cuh"
 
 namespace fermi {
@@ -359,18 +360,6 @@ cudaError_t launch_residual_plain(const StepArgs& a, const void* UT32, int64_t k
 }
 
 // ------------------------------------------------------------------------ draw + state update
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_inclusive_scan(double v, int lane) {
-  for (int o = 1; o < 32; o <<= 1) {
-    const double t = __shfl_up_sync(kFull, v, o);
-    if (lane >= o) v += t;
-  }
-  return v;
-}
-
 // One CTA (256 threads, 8 warps) per sample.
 //  (1) Z and the inverse CDF with a warp-shuffle block scan: warp w owns a contiguous
 //      segment of sites; segment totals give each warp its base; each warp then walks
@@ -385,99 +374,17 @@ template <typename S>
 __global__ void __launch_bounds__(256) tail_kernel(StepArgs a, int64_t k, int op_mode) {
   using Ud = typename std::conditional<is_cplx<S>::value, cd, double>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double s_wsum[8], s_wbase[8];
-  __shared__ int s_cand[8];
-  __shared__ int s_x;
-  __shared__ double s_Z;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int64_t b = blockIdx.x;
   const uint64_t sample = a.first + (uint64_t)b;
   const int64_t L = a.L, N = a.N;
   const float* __restrict__ prow = a.P + b * a.ldP;
 
-  // (1) normaliser and inverse CDF
-  const int64_t seg = ((L + 255) / 256) * 32;
-  const int64_t w0 = min(L, (int64_t)warp * seg), w1 = min(L, w0 + seg);
-  double ws = 0.0;
-  for (int64_t i = w0 + lane; i < w1; i += 32) ws += (double)prow[i];
-  ws = warp_sum(ws);
-  if (lane == 0) s_wsum[warp] = ws;
-  __syncthreads();
-  if (tid == 0) {
-    double acc = 0.0;
-    for (int w = 0; w < 8; ++w) {
-      s_wbase[w] = acc;
-      acc += s_wsum[w];
-    }
-    s_Z = acc;
-  }
-  __syncthreads();
-  const double Z = s_Z;
-  int x;
-  if (a.force_x) {
-    x = a.force_x[b * a.n_steps + k];
-    if (x < 0 || x >= L) {
-      if (tid == 0) set_status(a.status, FFS_E_ARG);
-      x = 0;
-    }
-  } else {
-    const double t = site_uniform(a.seed, sample, (int)k) * Z;
-    int cand = INT_MAX;
-    double carry = s_wbase[warp];
-    for (int64_t i0 = w0; i0 < w1; i0 += 32) {
-      const int64_t i = i0 + lane;
-      const double v = (i < w1) ? (double)prow[i] : 0.0;
-      const double inc = warp_inclusive_scan(v, lane);
-      const unsigned hit = __ballot_sync(kFull, (i < w1) && v > 0.0 && (carry + inc > t));
-      if (hit) {
-        cand = (int)(i0 + __ffs(hit) - 1);
-        break;
-      }
-      carry += __shfl_sync(kFull, inc, 31);
-    }
-    if (lane == 0) s_cand[warp] = cand;
-    __syncthreads();
-    if (tid == 0) {
-      int xs = INT_MAX;
-      for (int w = 0; w < 8; ++w) xs = min(xs, s_cand[w]);
-      s_x = xs;
-    }
-    __syncthreads();
-    x = s_x;
-    if (x == INT_MAX) {  // rounding left no site above t: the last site with weight
-      int last = -1;
-      for (int64_t i = tid; i < L; i += blockDim.x)
-        if (prow[i] > 0.f) last = (int)i;
-      for (int o = 16; o; o >>= 1) last = max(last, __shfl_xor_sync(kFull, last, o));
-      if (lane == 0) s_cand[warp] = last;
-      __syncthreads();
-      if (tid == 0) {
-        int l = -1;
-        for (int w = 0; w < 8; ++w) l = max(l, s_cand[w]);
-        s_x = l;
-      }
-      __syncthreads();
-      x = s_x;
-      if (x < 0) {
-        if (tid == 0) set_status(a.status, FFS_E_NUMERIC);
-        x = 0;
-      }
-    }
-  }
-
-  // (2) outputs
-  if (tid == 0) {
-    a.x[b * a.n_steps + k] = x;
-    a.mask[b * a.ldMask + (x >> 5)] |= 1u << (x & 31);
-    const double px = (double)prow[x];
-    a.logp[b] += (px > 0.0 && Z > 0.0) ? log(px / Z) : -INFINITY;
-    if (!(Z > 0.0) || !isfinite(Z)) set_status(a.status, FFS_E_NUMERIC);
-  }
-  if (a.probs) {
-    float* pr = a.probs + ((size_t)b * a.n_steps + k) * L;
-    const double iz = Z > 0.0 ? 1.0 / Z : 0.0;
-    for (int64_t i = tid; i < L; i += blockDim.x) pr[i] = (float)((double)prow[i] * iz);
-  }
+  // (1) normaliser and inverse CDF, (2) outputs
+  __shared__ DrawShared dsh;
+  double Z = 0.0;
+  const int x = block_draw(prow, L, a.seed, sample, k, forced_site(a, b, k), a.status, dsh, Z);
+  draw_outputs(a, b, k, x, Z, prow);
   if (k + 1 >= a.n_steps) return;
 
   // (3) state update

@@ -35,6 +35,27 @@ struct StepArgs {
   int* status;
 };
 
+// Precision of the per-sample elimination state.
+enum StateKind : int { kStateFP64 = 0, kStateFP32 = 1, kStateDF64 = 2 };
+
+// Buffers of the blocked state (per sample: W N x N, WsT N x 32, beta 32 x 32, piv 32).
+struct BlockedArgs {
+  int64_t Nc;  // state columns kept (= steps taken)
+  void* W;
+  void* WsT;
+  void* beta;
+  void* piv;
+};
+
+cudaError_t launch_blocked_step(const StepArgs& a, const BlockedArgs& t, int64_t k, int state, int op,
+                                cudaStream_t s);
+cudaError_t launch_blocked_panel(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int state,
+                                 int op, cudaStream_t s);
+size_t blocked_elem_bytes(bool cplx, int state);
+size_t blocked_step_smem(int64_t Nc, bool cplx, int state);
+int blocked_panel_width();
+cudaError_t configure_blocked();
+
 cudaError_t launch_perm_init(const StepArgs& a, int op_mode, cudaStream_t s);
 cudaError_t launch_ortho_check(const void* U64, bool cplx, int64_t L, int64_t N, double* maxdev,
                                cudaStream_t s);

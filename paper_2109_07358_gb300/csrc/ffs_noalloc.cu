@@ -9,8 +9,8 @@
 // memory, declared below.  The caller passes U and the output buffer; nothing else is
 // allocated, by this library or by any library it calls.
 //
-// The arithmetic is the same as ffs_sample_ex with FFS_RES_FP32 | FFS_STATE_FP64
-// (FP32 all-site weights over the real embedding of U, summed in the same order; FP64
+// The arithmetic is the same as ffs_sample_ex with FFS_RES_FP32 | FFS_STATE_FP64 |
+// FFS_TAIL_UNBLOCKED (FP32 all-site weights over the real embedding of U, summed in the same order; FP64
 // Gauss-Jordan elimination state; the same draw), fused into one kernel in which one
 // CTA runs the whole chain of one sample.  It is meant for small problems: the
 // per-sample working set must fit in the fixed array.

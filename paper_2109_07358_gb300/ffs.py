@@ -30,9 +30,11 @@ FFS_RES_BF16 = 0x2
 FFS_RES_TF32 = 0x3
 FFS_STATE_FP64 = 0x00
 FFS_STATE_FP32 = 0x10
+FFS_STATE_DF64 = 0x20
 FFS_FORM_BATCHED = 0x000
 FFS_FORM_PLAIN = 0x100
 FFS_NO_ORTHO_CHECK = 0x1000
+FFS_TAIL_UNBLOCKED = 0x2000
 
 _lib = None
 
@@ -147,9 +149,9 @@ def ffs_query(h, B: int = 0):
     return {"L": L.value, "N": N.value, "dtype": dt.value, "flags": fl.value, "bytes_for_B": bts.value}
 
 
-FFS_PHASE_PERM, FFS_PHASE_RESIDUAL, FFS_PHASE_TAIL = 0, 1, 2
-FFS_NUM_PHASES = 3
-PHASE_NAMES = ("perm", "residual", "tail")
+FFS_PHASE_PERM, FFS_PHASE_RESIDUAL, FFS_PHASE_TAIL, FFS_PHASE_PANEL = 0, 1, 2, 3
+FFS_NUM_PHASES = 4
+PHASE_NAMES = ("perm", "residual", "tail", "panel")
 
 
 def ffs_profile(h, enable: bool = True):

@@ -2,7 +2,9 @@
 
 Tolerances (absolute, on normalised conditional probabilities, teacher-forced on the
 oracle's prefix and column order so one divergent draw cannot cascade):
-  FP32 residual with FP64 state, and the plain per-sample FP32 form:   1e-6
+  FP32 residual with an FP64 or double-float state (the FP32 path):   1e-6
+  plain per-sample form (FP32 residual and FP32 state; its error grows
+  with N through the FP32 state: 1.3e-6 at N = 75):                    5e-6
   BF16x3 tensor-core residual (the batched mixed-precision form):      1e-4
   TF32 / BF16 single-product residuals (no accuracy target; bounds):   2e-3 / 2e-2
 Free-running draws must be identical to the oracle's except where the uniform lies
@@ -25,16 +27,22 @@ pytestmark = pytest.mark.gpu
 
 MODES = {
     "fp32": (ffs.FFS_RES_FP32 | ffs.FFS_STATE_FP64, 1e-6),
-    "plain": (ffs.FFS_FORM_PLAIN, 1e-6),
+    "fp32_df64": (ffs.FFS_RES_FP32 | ffs.FFS_STATE_DF64, 1e-6),
+    "fp32_unblocked": (ffs.FFS_RES_FP32 | ffs.FFS_STATE_FP64 | ffs.FFS_TAIL_UNBLOCKED, 1e-6),
+    "plain": (ffs.FFS_FORM_PLAIN, 5e-6),
     "bf16x3": (ffs.FFS_RES_BF16X3 | ffs.FFS_STATE_FP64, 1e-4),
+    "bf16x3_df64": (ffs.FFS_RES_BF16X3 | ffs.FFS_STATE_DF64, 1e-4),
+    "bf16x3_s32": (ffs.FFS_RES_BF16X3 | ffs.FFS_STATE_FP32, 1e-4),
     "tf32": (ffs.FFS_RES_TF32 | ffs.FFS_STATE_FP64, 2e-3),
     "bf16": (ffs.FFS_RES_BF16 | ffs.FFS_STATE_FP64, 2e-2),
 }
+TARGETED = ("fp32", "fp32_df64", "fp32_unblocked", "plain", "bf16x3", "bf16x3_df64", "bf16x3_s32")
 
 CASES = {
     "real": lambda: w.haar(300, 40, seed=1, complex_=False),
     "complex": lambda: w.haar(200, 30, seed=2),
     "lattice": lambda: w.square_lattice(8, 8, 16, seed=0),
+    "panels": lambda: w.haar(160, 75, seed=9),   # three 32-column panels, two trailing updates
 }
 B = 70      # two 64-sample tiles and a ragged tail
 SEED = 12345
@@ -114,11 +122,11 @@ def test_free_running_draws_match(case, mode):
     frac, bad = draw_identity(X, recs, eps=max(tol, 1e-6))
     print(f"{case} {mode}: identical {frac:.4f}, unexcused {bad}")
     assert not bad
-    if mode in ("fp32", "plain", "bf16x3"):   # the modes with an accuracy target
+    if mode in TARGETED:   # the modes with an accuracy target
         assert frac >= 0.95
 
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16x3", "plain"])
+@pytest.mark.parametrize("mode", ["fp32", "bf16x3", "bf16x3_df64", "plain"])
 def test_chain_L64_N8_full_batch(mode):
     """The small plain workload: open chain L = 64, N = 8, 10^4 samples, seed 0."""
     flags, tol = MODES[mode]
@@ -160,12 +168,14 @@ def test_brute_force_chi2_on_gpu_samples():
     assert stats.chisquare(obs, np.array(exp) * n / np.sum(exp)).pvalue > 0.01
 
 
-def test_marginal_prefix_and_sharding_invariance():
-    U = w.haar(256, 48, seed=7)
-    S = sampler(U, ffs.FFS_RES_BF16X3)
+@pytest.mark.parametrize("state", [ffs.FFS_STATE_FP64, ffs.FFS_STATE_DF64, ffs.FFS_STATE_FP32])
+def test_marginal_prefix_and_sharding_invariance(state):
+    U = w.haar(256, 70, seed=7)
+    S = sampler(U, ffs.FFS_RES_BF16X3 | state)
     full = S.sample(100, 3)["x"].cpu().numpy()
-    part = S.sample(100, 3, n_steps=17)["x"].cpu().numpy()
-    assert np.array_equal(full[:, :17], part)
+    for ns in (17, 32, 45):
+        part = S.sample(100, 3, n_steps=ns)["x"].cpu().numpy()
+        assert np.array_equal(full[:, :ns], part)
     a = S.sample(37, 3)["x"].cpu().numpy()
     b = S.sample(63, 3, first_sample_index=37)["x"].cpu().numpy()
     assert np.array_equal(np.concatenate([a, b]), full)

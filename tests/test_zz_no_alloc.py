@@ -3,7 +3,8 @@
 Such callers (a frozen memory pool, a framework allocator that must not be bypassed,
 a plugin limited to the memory it is given) cannot use ffs_create, which allocates.
 The allocation-free entry point works in a fixed array inside the library and must
-give the same samples as ffs_sample_ex with FFS_RES_FP32 | FFS_STATE_FP64, within
+give the same samples as ffs_sample_ex with FFS_RES_FP32 | FFS_STATE_FP64 |
+FFS_TAIL_UNBLOCKED, within
 the tolerance the parity tests use: draws identical except where the uniform lies
 within 1e-6 of an oracle CDF boundary.  Two calls in a row check that the contents a
 previous call leaves in the shared array do not leak into the next one.
@@ -39,7 +40,7 @@ def _check_against_sample_ex(U, B, seed):
     out = torch.full((B, N), -1, dtype=torch.int32, device="cuda")
     ffs.ffs_sample_noalloc(Ud, ffs.dtype_of(Ud), L, N, B, seed, out)
     torch.cuda.synchronize()
-    S = ffs.Sampler(Ud, ffs.FFS_RES_FP32 | ffs.FFS_STATE_FP64)
+    S = ffs.Sampler(Ud, ffs.FFS_RES_FP32 | ffs.FFS_STATE_FP64 | ffs.FFS_TAIL_UNBLOCKED)
     ref = S.sample(B, seed)["x"]
     S.sync()
     S.close()
