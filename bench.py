@@ -32,6 +32,10 @@ WORKLOADS = {
         make="lattice", B=4096, L=4096, N=1024, cplx=True,
         desc="64x64 open square lattice, random U(1) hopping phases (seed 0), N=1024 lowest orbitals, "
              "complex, B=4096 samples, Philox seed 0"),
+    "lattice32x32_N256_B1024": dict(
+        make="lattice32", B=1024, L=1024, N=256, cplx=True,
+        desc="32x32 open square lattice, random U(1) hopping phases (seed 0), N=256 lowest orbitals, "
+             "complex, B=1024 samples, Philox seed 0 (reduced case for profiler captures)"),
     "chain64_N8_B10000": dict(
         make="chain", B=10000, L=64, N=8, cplx=False,
         desc="1D open chain L=64, N=8 (closed-form orbitals), B=10^4 samples, Philox seed 0"),
@@ -58,6 +62,8 @@ def make_U(spec):
 
     if spec["make"] == "lattice":
         return w.lattice_64x64_N1024(0)
+    if spec["make"] == "lattice32":
+        return w.square_lattice(32, 32, 256, 0)
     if spec["make"] == "chain":
         return w.chain_L64_N8()
     raise ValueError(spec["make"])
@@ -258,10 +264,10 @@ def main():
     stream = torch.cuda.Stream()
     S = ffs.Sampler(U, flags, stream=stream)
     x = torch.empty((B, N), dtype=torch.int32, device="cuda")
-    first = rank * B * (args.steps + args.warmup + 1)
+    from paper_2109_07358_gb300.shard import step_offset
 
     def step(i):
-        ffs.ffs_sample_ex(S.h, B, 0, first + i * B, 0, x, stream=stream)
+        ffs.ffs_sample_ex(S.h, B, 0, step_offset(i, rank, world, B), 0, x, stream=stream)
 
     for i in range(args.warmup):
         step(i)
@@ -372,7 +378,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = ffs.ffs_create_ex(U_host, ffs.dtype_of(U_host), L, N, N, flags, stream)
-            ffs.ffs_sample_ex(h, B, 0, first + i * B, 0, x_host, stream=stream)
+            ffs.ffs_sample_ex(h, B, 0, step_offset(i, rank, world, B), 0, x_host, stream=stream)
             ffs.ffs_destroy(h)
             times.append(time.perf_counter() - t0)
         e2e_s = float(np.median(times[1:]))
