@@ -207,6 +207,94 @@ def run_reference(args, spec, rank, world):
     return 0
 
 
+# ------------------------------------------------------------------------------ patterns
+def bench_batching(args, flags, stream):
+    """Many independent instances (Haar U, L log-uniform in [256, 8192], N log-uniform in
+    [16, min(1024, L/4)], 64 samples each): one grouped, graph-captured schedule against
+    the same instances sampled one after another."""
+    import torch
+
+    from paper_2109_07358_gb300 import ffs
+    from paper_2109_07358_gb300 import workloads as w
+
+    sizes = w.batch_sizes(args.instances, seed=0)
+    Ss, outs = [], []
+    for i, (L, N) in enumerate(sizes):
+        U = w.haar_torch(L, N, seed=i)
+        Ss.append(ffs.Sampler(U, flags, stream=stream))
+        outs.append(torch.empty((64, N), dtype=torch.int32, device="cuda"))
+    hs = [S.h for S in Ss]
+    Bs = [64] * len(Ss)
+    seeds = list(range(len(Ss)))
+
+    def grouped():
+        ffs.ffs_sample_batched(hs, Bs, seeds, outs, stream=stream)
+
+    def sequential():
+        for S, o, sd in zip(Ss, outs, seeds):
+            ffs.ffs_sample_ex(S.h, 64, sd, 0, 0, o, stream=stream)
+
+    res = {}
+    for name, fn in (("grouped", grouped), ("sequential", sequential)):
+        fn()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        res[name] = {"ms": e0.elapsed_time(e1), "wall_ms": 1e3 * (time.perf_counter() - t0)}
+    total = 64 * len(Ss)
+    flops = sum(flops_per_sample(L, N, True) for L, N in sizes) * 64
+    for S in Ss:
+        S.close()
+    return {"workload": f"{len(Ss)} Haar complex instances, L log-uniform [256, 8192], N log-uniform "
+                        f"[16, min(1024, L/4)], 64 samples each",
+            "samples": total, "grouped_samples_per_s": total / (res["grouped"]["ms"] / 1e3),
+            "sequential_samples_per_s": total / (res["sequential"]["ms"] / 1e3),
+            "grouped_over_sequential": res["sequential"]["ms"] / res["grouped"]["ms"],
+            "grouped_ms": res["grouped"]["ms"], "sequential_ms": res["sequential"]["ms"],
+            "residual_algorithmic_tflops": flops / (res["grouped"]["ms"] / 1e3) / 1e12,
+            "launch": "one CUDA graph of grouped launches"}
+
+
+def bench_serving(args, flags):
+    """Poisson stream of projection-DPP requests (U = top-N left singular vectors of L
+    unit-norm Gaussian features of dimension D; L log-uniform [500, 20000], D in [64, 512],
+    N in [5, min(200, D)], 1-32 samples) into the continuous-batching engine."""
+    import numpy as np
+    import torch
+
+    from paper_2109_07358_gb300 import ffs
+    from paper_2109_07358_gb300 import workloads as w
+
+    sizes = w.serving_requests(args.requests, seed=0)
+    Us = [w.lensemble_orbitals_torch(L, D, N, seed=1000 + i).cpu().numpy() for i, (L, D, N, _) in enumerate(sizes)]
+    outs = [np.empty((s, N), dtype=np.int32) for (L, D, N, s) in sizes]
+    rng = np.random.default_rng(1)
+    gaps = rng.exponential(1.0 / args.rate, size=len(sizes))
+    srv = ffs.ffs_server_create(0, flags, 0)
+    ids = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for i, (L, D, N, s) in enumerate(sizes):
+        t_next += gaps[i]
+        while time.perf_counter() < t_next:
+            time.sleep(0.0002)
+        ids.append(ffs.ffs_submit(srv, Us[i], ffs.FFS_F64, L, N, s, 7 + i, outs[i]))
+    lat = [ffs.ffs_wait(srv, rid, 600_000) for rid in ids]
+    wall = time.perf_counter() - t0
+    stats = ffs.ffs_server_stats(srv)
+    ffs.ffs_server_destroy(srv)
+    samples = sum(s for (_, _, _, s) in sizes)
+    return {"workload": f"{len(sizes)} Poisson requests at {args.rate:g}/s, L log-uniform [500, 20000], "
+                        f"D uniform [64, 512], N uniform [5, min(200, D)], 1-32 samples",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(np.mean(lat)), "samples_per_s": samples / wall, "requests": len(sizes),
+            "engine_iterations": stats["iterations"]}
+
+
 # ------------------------------------------------------------------------------ GPU path
 def main():
     ap = argparse.ArgumentParser()
@@ -222,6 +310,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-samples", type=int, default=0)
+    ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=300.0, help="serving arrivals per second")
     args = ap.parse_args()
     spec = dict(WORKLOADS[args.workload])
     if args.B:
@@ -323,11 +416,12 @@ def main():
     dominant = "tail" if tail_all >= res_ms else "residual"
     if dominant == "tail":
         ach = tail_fl / (tail_all / 1e3) / 1e12
-        # state flops per FP32-pipe op: 1 (FP32 FMA = 2 flops / 2), double-float about 1/6
+        # a double-float multiply-add takes about 12 FP32-pipe instructions (exact product of
+        # the high parts by FMA, cross terms, error-free sum), so its peak is FP32 / 12
         peak, src = {"fp64": (NOMINAL_FP64_TFLOPS, "nominal FP64 rate (1.25 TFLOP/s)"),
-                     "fp32": (NOMINAL_FP32_TFLOPS, "nominal FP32 rate"),
-                     "df64": (NOMINAL_FP32_TFLOPS / 6, "nominal FP32 rate / 6 (double-float multiply-add "
-                              "= 6 FP32 FMA-equivalents)")}[args.state]
+                     "fp32": (NOMINAL_FP32_TFLOPS, "nominal FP32 rate (152 SMs x 128 lanes x 2 x 2.07 GHz)"),
+                     "df64": (NOMINAL_FP32_TFLOPS / 12, "nominal FP32 rate / 12 (FP32-pipe instructions per "
+                              "double-float multiply-add)")}[args.state]
         roof = {"kernel": f"state update ({args.state}, per-step + per-panel)", "bound": "alu", "achieved": ach,
                 "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_source": src}
     else:
@@ -394,6 +488,10 @@ def main():
                                          f"{wall:.1f} s wall"}
 
     S.close()
+    if not args.no_batching and rank == 0:
+        out["batching"] = bench_batching(args, flags, stream)
+    if not args.no_serving and rank == 0:
+        out["serving"] = bench_serving(args, flags)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

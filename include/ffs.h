@@ -116,7 +116,9 @@ int ffs_create(const double* U, int64_t L, int64_t N, ffs_handle* out);
 /*
  * ffs_create_ex - as ffs_create with an element type, a leading dimension ldU >= N
  * (in elements), flags (above) and a CUDA stream (cudaStream_t, NULL = legacy default
- * stream) on which every later call of this handle is ordered.
+ * stream) on which every later call of this handle is ordered.  A device U is read on
+ * that stream: work that produces it on another stream must be complete or ordered
+ * before it (e.g. with an event).
  */
 int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, unsigned flags,
                   void* cuda_stream, ffs_handle* out);
@@ -197,6 +199,46 @@ int ffs_query(ffs_handle h, int64_t* L, int64_t* N, int* dtype, unsigned* flags,
 #define FFS_NOALLOC_SCRATCH_BYTES (16u << 20)
 int ffs_sample_noalloc(const void* U, int dtype, int64_t L, int64_t N, int64_t B, uint64_t seed,
                        int32_t* out_x, void* cuda_stream);
+
+/*
+ * ffs_sample_batched - sample many independent instances together (the batching
+ * pattern: many U of uneven L and N).  Instance i draws Bs[i] samples of handle hs[i]
+ * with seed seeds[i] (sample indices 0..Bs[i]-1) into the device buffer outs[i]
+ * (Bs[i] x N_i int32).  All instances advance step by step through grouped launches
+ * (one kernel launch serves every instance still running), and the whole schedule is
+ * captured once into a CUDA graph and launched as one graph on cuda_stream.  The
+ * samples are identical to separate ffs_sample calls.  All handles must use the batched
+ * tensor-core form with the blocked state, the same flags and the same real/complex
+ * type; a handle may appear once; every instance's wave must fit in memory at once.
+ * Asynchronous; errors of the set-up are returned, device errors surface at ffs_sync
+ * of the handles.
+ */
+int ffs_sample_batched(ffs_handle* hs, const int64_t* Bs, const uint64_t* seeds, int32_t** outs, int n,
+                       void* cuda_stream);
+
+/*
+ * Serving engine (continuous batching).  Requests with their own U, L, N, sample count
+ * and seed arrive at any time (ffs_submit copies U, so the caller may free it on
+ * return).  A host thread admits queued requests in arrival order while their device
+ * footprint (copies of U, operand, per-sample state and buffers) fits the HBM budget
+ * and an active slot is free; every engine iteration advances each active request by
+ * one step with grouped launches, so requests at different steps share the GPU and a
+ * new request starts while older ones are mid-chain.  A request's samples are the same
+ * as a standalone ffs_sample of its U and seed.  ffs_wait blocks until the request is
+ * done (timeout_ms < 0: no limit; FFS_E_TIMEOUT when it runs out) and reports the
+ * latency from submission to completion.
+ *   hbm_budget   bytes the engine may hold for requests; 0 = 80% of free memory.
+ *   flags        as ffs_create_ex; the tensor-core residual and the blocked state.
+ *   max_active   requests in flight at once (<= 0: no limit besides memory).
+ *   out_x        host or device, n_samples x N int32, written before ffs_wait returns.
+ */
+typedef struct ffs_server ffs_server;
+int ffs_server_create(size_t hbm_budget, unsigned flags, int max_active, void* cuda_stream, ffs_server** out);
+int ffs_submit(ffs_server* s, const void* U, int dtype, int64_t L, int64_t N, int64_t n_samples, uint64_t seed,
+               int32_t* out_x, uint64_t* req_id);
+int ffs_wait(ffs_server* s, uint64_t req_id, int timeout_ms, double* latency_ms);
+int ffs_server_stats(ffs_server* s, int64_t* pending, int64_t* active, int64_t* iterations, size_t* bytes_in_use);
+void ffs_server_destroy(ffs_server* s);
 
 /* Phases reported by ffs_profile_read. */
 #define FFS_PHASE_PERM 0      /* column orders m and the step-0 operand              */

@@ -2,6 +2,7 @@
 // The declarations and the contract of every entry point are in include/ffs.h.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "ffs_kernels.cuh"
@@ -265,12 +266,17 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
   } while (0)
   CREATE_TRY(cudaGetDevice(&c->device));
   CREATE_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-  static bool configured = false;
-  if (!configured) {
-    CREATE_TRY(configure_kernels(N, cplx));
-    CREATE_TRY(configure_residual_tc());
-    CREATE_TRY(configure_blocked());
-    configured = true;
+  {
+    // Kernel attributes are set once per device (callers may create handles from several threads).
+    static std::mutex mu;
+    static bool configured[64] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    if (c->device >= 0 && c->device < 64 && !configured[c->device]) {
+      CREATE_TRY(configure_kernels(N, cplx));
+      CREATE_TRY(configure_residual_tc());
+      CREATE_TRY(configure_blocked());
+      configured[c->device] = true;
+    }
   }
   c->Lr = cplx ? 2 * L : L;
   c->Kr = cplx ? 2 * N : N;
@@ -495,6 +501,21 @@ int ffs_sync(ffs_handle h) {
 }
 
 void ffs_destroy(ffs_handle h) { release(h); }
+
+}  // extern "C"
+
+namespace fermi {
+int ctx_op_mode(const ffs_ctx* c) { return op_mode_of(c->flags); }
+int ctx_state_kind(const ffs_ctx* c) { return state_kind(c); }
+bool ctx_blocked(const ffs_ctx* c) { return blocked(c); }
+int ctx_ensure_workspace(ffs_ctx* c, int64_t B) { return ensure_workspace(c, B); }
+size_t ctx_per_sample_bytes(const ffs_ctx* c) { return per_sample_bytes(c); }
+size_t ctx_op_elem_bytes(int op) { return op_elem_bytes(op); }
+int ctx_fail(ffs_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
+bool ptr_is_device(const void* p) { return is_device_ptr(p); }
+}  // namespace fermi
+
+extern "C" {
 
 int ffs_profile(ffs_handle h, int enable) {
   if (!h) return fail(nullptr, FFS_E_ARG, "ffs_profile: NULL handle");

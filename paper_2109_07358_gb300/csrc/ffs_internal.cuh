@@ -192,3 +192,16 @@ struct ffs_ctx {
   double prof_ms[8] = {0};
   int64_t prof_launches[8] = {0};
 };
+
+namespace fermi {
+// Handle internals shared by the C-ABI file and the multi-instance engine.
+int ctx_op_mode(const ffs_ctx* c);
+int ctx_state_kind(const ffs_ctx* c);
+bool ctx_blocked(const ffs_ctx* c);
+int ctx_ensure_workspace(ffs_ctx* c, int64_t B);
+size_t ctx_per_sample_bytes(const ffs_ctx* c);
+size_t ctx_op_elem_bytes(int op);
+int ctx_fail(ffs_ctx* c, int code, const std::string& msg);
+bool ptr_is_device(const void* p);
+void set_null_handle_error(const std::string& msg);
+}  // namespace fermi

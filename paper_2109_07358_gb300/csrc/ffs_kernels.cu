@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "ffs_draw.cuh"
+#include "ffs_group.cuh"
 #include "ffs_kernels.cuh"
 
 namespace fermi {
@@ -76,9 +77,7 @@ __device__ __forceinline__ void put_operand(const StepArgs& a, int op, int64_t b
 // One thread per sample: Fisher-Yates over (0..N-1) driven by Philox stream 0 (block j
 // serves shuffle steps N-1-2j and N-2-2j, 64 bits each, index = mulhi(r, i+1)).  Also
 // writes the step-0 operand h = e_{m_0} (the operand buffer is zeroed beforehand).
-__global__ void perm_init_kernel(StepArgs a, int op_mode) {
-  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (b >= a.bw) return;
+__device__ __forceinline__ void perm_one(const StepArgs& a, int op_mode, int64_t b) {
   const uint64_t sample = a.first + (uint64_t)b;
   int32_t* m = const_cast<int32_t*>(a.m) + b * a.N;
   for (int64_t i = 0; i < a.N; ++i) m[i] = (int32_t)i;
@@ -110,6 +109,42 @@ __global__ void perm_init_kernel(StepArgs a, int op_mode) {
     else
       put_operand(a, op_mode, b, m[0], 1.0);
   }
+}
+
+__global__ void perm_init_kernel(StepArgs a, int op_mode) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= a.bw) return;
+  perm_one(a, op_mode, b);
+}
+
+// Grouped start of a wave: per sample, clear its operand row, drawn-site bits and
+// log-probability, then draw its column order (128 samples per CTA).
+__global__ void group_init_kernel(const GroupInst* __restrict__ inst, const GroupEntry* __restrict__ ent, int n,
+                                  int op_mode) {
+  const int64_t item = blockIdx.x;
+  const int e = group_find(ent, n, item);
+  const StepArgs a = inst[ent[e].inst].a;
+  const int64_t b = (item - ent[e].start) * 128 + threadIdx.x;
+  if (b >= a.bw) return;
+  if (op_mode == kOpF32 || op_mode == kOpTF32) {
+    float* h = (float*)a.H + b * a.Kp;
+    for (int64_t i = 0; i < a.Kp; ++i) h[i] = 0.f;
+  } else if (op_mode == kOpBF16x3 || op_mode == kOpBF16) {
+    __nv_bfloat16* h = (__nv_bfloat16*)a.H + b * a.Kp;
+    for (int64_t i = 0; i < a.Kp; ++i) h[i] = __float2bfloat16(0.f);
+    if (op_mode == kOpBF16x3)
+      for (int64_t i = 0; i < a.Kp; ++i) h[a.hplane + i] = __float2bfloat16(0.f);
+  }
+  for (int64_t i = 0; i < a.ldMask; ++i) a.mask[b * a.ldMask + i] = 0u;
+  a.logp[b] = 0.0;
+  perm_one(a, op_mode, b);
+}
+
+cudaError_t launch_group_init(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op,
+                              cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  group_init_kernel<<<(unsigned)total, 128, 0, s>>>(inst, e, n, op);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_perm_init(const StepArgs& a, int op_mode, cudaStream_t s) {

@@ -20,21 +20,13 @@
 // lanes of its rank mod 4).
 #include <cudaTypedefs.h>
 
+#include "ffs_group.cuh"
 #include "ffs_residual_tc.cuh"
 #include "ffs_sm100.cuh"
 
 namespace fermi {
 
 using namespace sm100;
-
-struct TcArgs {
-  int64_t bw, L, ldP, ldMask;
-  int nK;
-  int cplx;
-  float* P;
-  const uint32_t* mask;
-  int* status;
-};
 
 enum { kKindBF16x3 = 0, kKindBF16 = 1, kKindTF32 = 2 };
 
@@ -51,13 +43,17 @@ struct TcCfg {
   static constexpr uint32_t IDESC = (KIND == kKindTF32) ? idesc_tf32(BM, BN) : idesc_bf16(BM, BN);
 };
 
+// One output tile (samples [b0, b0+128) x embedding columns [j0, j0+BN)) of one
+// instance; the tensor maps may live in kernel parameters or in global memory.
 template <int BN, int STAGES, int KIND>
-__global__ void __launch_bounds__(192, 1)
-    residual_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
-                       const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
-                       TcArgs p) {
+__device__ __forceinline__ void residual_body(const CUtensorMap* tmA0p, const CUtensorMap* tmA1p,
+                                              const CUtensorMap* tmB0p, const CUtensorMap* tmB1p, const TcArgs& p,
+                                              int32_t b0, int32_t j0, uint8_t* smem_raw, bool global_maps) {
   using C = TcCfg<BN, STAGES, KIND>;
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const CUtensorMap& tmA0 = *tmA0p;
+  const CUtensorMap& tmA1 = *tmA1p;
+  const CUtensorMap& tmB0 = *tmB0p;
+  const CUtensorMap& tmB1 = *tmB1p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -87,13 +83,16 @@ __global__ void __launch_bounds__(192, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
-  const int32_t b0 = (int32_t)blockIdx.y * C::BM;
-  const int32_t j0 = (int32_t)blockIdx.x * BN;
   const int nK = p.nK;
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer
+    if (global_maps) {
+      acquire_tmap(&tmA0);
+      acquire_tmap(&tmA1);
+      acquire_tmap(&tmB0);
+      acquire_tmap(&tmB1);
+    }
     prefetch_tmap(&tmA0);
     prefetch_tmap(&tmB0);
     if (C::NA == 2) {
@@ -216,6 +215,31 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+template <int BN, int STAGES, int KIND>
+__global__ void __launch_bounds__(192, 1)
+    residual_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+                       const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
+                       TcArgs p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  residual_body<BN, STAGES, KIND>(&tmA0, &tmA1, &tmB0, &tmB1, p, (int32_t)blockIdx.y * 128,
+                                  (int32_t)blockIdx.x * BN, smem_raw, false);
+}
+
+// Grouped form: CTA blockIdx.x -> (instance, tile) through the entry list.
+template <int BN, int STAGES, int KIND>
+__global__ void __launch_bounds__(192, 1)
+    residual_group_kernel(const GroupInst* __restrict__ inst, const GroupEntry* __restrict__ ent, int n) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const int64_t item = blockIdx.x;
+  const int e = group_find(ent, n, item);
+  const GroupInst* gi = inst + ent[e].inst;
+  const int64_t local = item - ent[e].start;
+  const int64_t bt = local / gi->n_jtiles, jt = local - bt * gi->n_jtiles;
+  const TcArgs p = gi->tc;
+  residual_body<BN, STAGES, KIND>(&gi->tm[0], &gi->tm[1], &gi->tm[2], &gi->tm[3], p, (int32_t)(bt * 128),
+                                  (int32_t)(jt * BN), smem_raw, true);
+}
+
 // ------------------------------------------------------------------ host side
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -306,7 +330,41 @@ cudaError_t launch_residual_tc(ffs_ctx* c, const StepArgs& a, int op, cudaStream
   }
 }
 
+cudaError_t launch_group_residual(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op,
+                                  cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)total;
+  switch (op) {
+    case kOpBF16x3:
+      residual_group_kernel<kBN, 2, kKindBF16x3><<<grid, 192, TcCfg<kBN, 2, kKindBF16x3>::SMEM, s>>>(inst, e, n);
+      break;
+    case kOpBF16:
+      residual_group_kernel<kBN, 4, kKindBF16><<<grid, 192, TcCfg<kBN, 4, kKindBF16>::SMEM, s>>>(inst, e, n);
+      break;
+    case kOpTF32:
+      residual_group_kernel<kBN, 4, kKindTF32><<<grid, 192, TcCfg<kBN, 4, kKindTF32>::SMEM, s>>>(inst, e, n);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int residual_tile_cols() { return kBN; }
+int residual_k_block(int op) { return op == kOpTF32 ? 32 : 64; }
+
 cudaError_t configure_residual_tc() {
+  {
+    cudaError_t e = cudaFuncSetAttribute(residual_group_kernel<kBN, 2, kKindBF16x3>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<kBN, 2, kKindBF16x3>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(residual_group_kernel<kBN, 4, kKindBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcCfg<kBN, 4, kKindBF16>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(residual_group_kernel<kBN, 4, kKindTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcCfg<kBN, 4, kKindTF32>::SMEM);
+    if (e != cudaSuccess) return e;
+  }
   cudaError_t e;
   e = cudaFuncSetAttribute(residual_tc_kernel<kBN, 2, kKindBF16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            TcCfg<kBN, 2, kKindBF16x3>::SMEM);

@@ -49,6 +49,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 }
 
 // ------------------------------------------------------------------ TMA
+// A tensor map that was written through the generic proxy (host copies into global
+// memory) must be acquired by the tensor-map proxy before TMA uses it.
+__device__ __forceinline__ void acquire_tmap(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)map) : "memory");
+}
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }

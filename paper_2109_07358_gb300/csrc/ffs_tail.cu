@@ -25,6 +25,7 @@
 
 #include "ffs_arith.cuh"
 #include "ffs_draw.cuh"
+#include "ffs_group.cuh"
 #include "ffs_kernels.cuh"
 
 namespace fermi {
@@ -59,14 +60,13 @@ __device__ __forceinline__ void put_h(const StepArgs& a, int op, int64_t b, int 
   put_out(a, op, b, 2 * col + 1, v.im);
 }
 
+// Step k of sample b of one instance, executed by one 256-thread CTA.
 template <typename A>
-__global__ void __launch_bounds__(256) tail_step_kernel(StepArgs a, BlockedArgs t, int64_t k, int op_mode) {
+__device__ __forceinline__ void step_body(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k,
+                                          int op_mode, unsigned char* smem_raw, DrawShared& dsh) {
   using T = Ar<A>;
   using U = typename T::U;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ DrawShared dsh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t b = blockIdx.x;
   const int64_t N = a.N, Nc = t.Nc;
   const float* __restrict__ prow = a.P + b * a.ldP;
 
@@ -147,13 +147,19 @@ __global__ void __launch_bounds__(256) tail_step_kernel(StepArgs a, BlockedArgs 
   }
 }
 
-// Trailing update of one sample (blockIdx.y) on 32 columns (blockIdx.x) of T = [k1, Nc).
 template <typename A>
-__global__ void __launch_bounds__(256) tail_panel_kernel(StepArgs a, BlockedArgs t, int64_t k0, int64_t k1,
-                                                         int op_mode) {
+__global__ void __launch_bounds__(256) tail_step_kernel(StepArgs a, BlockedArgs t, int64_t k, int op_mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ DrawShared dsh;
+  step_body<A>(a, t, blockIdx.x, k, op_mode, smem_raw, dsh);
+}
+
+// Trailing update of sample b on the 32 columns cb of T = [k1, Nc), one 256-thread CTA.
+template <typename A>
+__device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t cb,
+                                           int64_t k0, int64_t k1, int op_mode, unsigned char* smem_raw) {
   using T = Ar<A>;
   using U = typename T::U;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   A* Ys = (A*)smem_raw;         // NB x 32: Y, then n
   A* Cs = Ys + NB * 32;         // NB x 32: U[x_new, m_j] chunk
   A* Ws = Cs + NB * 32;         // 32 x 32: W chunk
@@ -162,10 +168,9 @@ __global__ void __launch_bounds__(256) tail_panel_kernel(StepArgs a, BlockedArgs
   int* xs = (int*)(ps + NB);    // NB new sites
   int* mj = xs + NB;            // 32: m of the current K chunk
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t b = blockIdx.y;
   const int64_t N = a.N, Nc = t.Nc;
   const int nbr = (int)(k1 - k0);
-  const int64_t c0 = k1 + (int64_t)blockIdx.x * 32;
+  const int64_t c0 = k1 + cb * 32;
   const int64_t c = c0 + lane;
   const bool cval = c < Nc;
   A* W = (A*)t.W + (size_t)b * N * N;
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(256) tail_panel_kernel(StepArgs a, BlockedArgs
   __syncthreads();
 
   // operand of step k1 (its column is the first of T)
-  if (op_mode != kOpNone && blockIdx.x == 0 && k1 < a.n_steps) {
+  if (op_mode != kOpNone && cb == 0 && k1 < a.n_steps) {
     for (int64_t j = tid; j <= k1; j += blockDim.x) {
       const A v = (j < k1) ? T::neg(W[j * N + k1]) : T::one();
       put_h(a, op_mode, b, mrow[j], T::out(v));
@@ -249,13 +254,90 @@ __global__ void __launch_bounds__(256) tail_panel_kernel(StepArgs a, BlockedArgs
   }
 }
 
+template <typename A>
+__global__ void __launch_bounds__(256) tail_panel_kernel(StepArgs a, BlockedArgs t, int64_t k0, int64_t k1,
+                                                         int op_mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  panel_body<A>(a, t, blockIdx.y, blockIdx.x, k0, k1, op_mode, smem_raw);
+}
+
+static size_t step_smem(int64_t Nc, size_t es) { return (size_t)Nc * (2 * es + 4) + (8 * 32 + 32) * es; }
+static size_t panel_smem(size_t es) { return (size_t)(NB * 32 * 2 + 32 * 32 + NB * NB + NB) * es + (NB + 32) * 4; }
+
+// Grouped forms: CTA blockIdx.x -> (instance, sample[, column block]) through the entry list.
+template <typename A>
+__global__ void __launch_bounds__(256)
+    step_group_kernel(const GroupInst* __restrict__ inst, const GroupEntry* __restrict__ ent, int n, int op_mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ DrawShared dsh;
+  const int64_t item = blockIdx.x;
+  const int e = group_find(ent, n, item);
+  const GroupInst* gi = inst + ent[e].inst;
+  const StepArgs a = gi->a;
+  const BlockedArgs t = gi->t;
+  step_body<A>(a, t, item - ent[e].start, ent[e].k, op_mode, smem_raw, dsh);
+}
+
+template <typename A>
+__global__ void __launch_bounds__(256)
+    panel_group_kernel(const GroupInst* __restrict__ inst, const GroupEntry* __restrict__ ent, int n, int op_mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t item = blockIdx.x;
+  const int e = group_find(ent, n, item);
+  const GroupInst* gi = inst + ent[e].inst;
+  const StepArgs a = gi->a;
+  const BlockedArgs t = gi->t;
+  const int64_t k = ent[e].k;
+  const int64_t k0 = (k / NB) * NB, k1 = min(k0 + NB, t.Nc);
+  const int64_t ncb = (t.Nc - k1 + 31) / 32;
+  const int64_t local = item - ent[e].start;
+  panel_body<A>(a, t, local / ncb, local % ncb, k0, k1, op_mode, smem_raw);
+}
+
+template <typename A>
+static cudaError_t group_step_t(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op,
+                                int64_t maxNc, cudaStream_t s) {
+  step_group_kernel<A><<<(unsigned)total, 256, step_smem(maxNc, sizeof(A)), s>>>(inst, e, n, op);
+  return cudaGetLastError();
+}
+template <typename A>
+static cudaError_t group_panel_t(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op,
+                                 cudaStream_t s) {
+  panel_group_kernel<A><<<(unsigned)total, 256, panel_smem(sizeof(A)), s>>>(inst, e, n, op);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_step(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, bool cplx,
+                              int state, int op, int64_t maxNc, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  if (cplx) {
+    if (state == kStateFP64) return group_step_t<cd>(inst, e, n, total, op, maxNc, s);
+    if (state == kStateFP32) return group_step_t<cf>(inst, e, n, total, op, maxNc, s);
+    return group_step_t<cdf>(inst, e, n, total, op, maxNc, s);
+  }
+  if (state == kStateFP64) return group_step_t<double>(inst, e, n, total, op, maxNc, s);
+  if (state == kStateFP32) return group_step_t<float>(inst, e, n, total, op, maxNc, s);
+  return group_step_t<df>(inst, e, n, total, op, maxNc, s);
+}
+
+cudaError_t launch_group_panel(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, bool cplx,
+                               int state, int op, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  if (cplx) {
+    if (state == kStateFP64) return group_panel_t<cd>(inst, e, n, total, op, s);
+    if (state == kStateFP32) return group_panel_t<cf>(inst, e, n, total, op, s);
+    return group_panel_t<cdf>(inst, e, n, total, op, s);
+  }
+  if (state == kStateFP64) return group_panel_t<double>(inst, e, n, total, op, s);
+  if (state == kStateFP32) return group_panel_t<float>(inst, e, n, total, op, s);
+  return group_panel_t<df>(inst, e, n, total, op, s);
+}
+
 size_t blocked_elem_bytes(bool cplx, int state) {
   const size_t base = (state == kStateFP32) ? 4 : 8;  // FP64 and double-float are both 8 bytes
   return cplx ? 2 * base : base;
 }
 
-static size_t step_smem(int64_t Nc, size_t es) { return (size_t)Nc * (2 * es + 4) + (8 * 32 + 32) * es; }
-static size_t panel_smem(size_t es) { return (size_t)(NB * 32 * 2 + 32 * 32 + NB * NB + NB) * es + (NB + 32) * 4; }
 
 template <typename A>
 static cudaError_t launch_step_t(const StepArgs& a, const BlockedArgs& t, int64_t k, int op, cudaStream_t s) {
@@ -322,6 +404,18 @@ cudaError_t configure_blocked() {
   if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<cd>, optin);
   if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<cf>, optin);
   if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<cdf>, optin);
+  if (e == cudaSuccess) e = allow_smem(step_group_kernel<double>, optin);
+  if (e == cudaSuccess) e = allow_smem(step_group_kernel<float>, optin);
+  if (e == cudaSuccess) e = allow_smem(step_group_kernel<df>, optin);
+  if (e == cudaSuccess) e = allow_smem(step_group_kernel<cd>, optin);
+  if (e == cudaSuccess) e = allow_smem(step_group_kernel<cf>, optin);
+  if (e == cudaSuccess) e = allow_smem(step_group_kernel<cdf>, optin);
+  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<double>, optin);
+  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<float>, optin);
+  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<df>, optin);
+  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<cd>, optin);
+  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<cf>, optin);
+  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<cdf>, optin);
   return e;
 }
 

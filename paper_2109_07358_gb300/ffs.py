@@ -65,10 +65,20 @@ def lib() -> ctypes.CDLL:
         L.ffs_query.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                 ctypes.POINTER(ctypes.c_uint), i64, ctypes.POINTER(i64)]
         L.ffs_sample_noalloc.argtypes = [vp, i32, i64, i64, i64, u64, vp, vp]
+        L.ffs_sample_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(u64),
+                                         ctypes.POINTER(vp), i32, vp]
+        L.ffs_server_create.argtypes = [ctypes.c_size_t, ctypes.c_uint, i32, vp, ctypes.POINTER(vp)]
+        L.ffs_submit.argtypes = [vp, vp, i32, i64, i64, i64, u64, vp, ctypes.POINTER(u64)]
+        L.ffs_wait.argtypes = [vp, u64, i32, ctypes.POINTER(ctypes.c_double)]
+        L.ffs_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                       ctypes.POINTER(ctypes.c_size_t)]
+        L.ffs_server_destroy.argtypes = [vp]
+        L.ffs_server_destroy.restype = None
         L.ffs_profile.argtypes = [vp, i32]
         L.ffs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]
         for name in ("ffs_create", "ffs_create_ex", "ffs_sample", "ffs_sample_ex", "ffs_sync", "ffs_query",
-                     "ffs_profile", "ffs_profile_read", "ffs_sample_noalloc"):
+                     "ffs_profile", "ffs_profile_read", "ffs_sample_noalloc", "ffs_sample_batched",
+                     "ffs_server_create", "ffs_submit", "ffs_wait", "ffs_server_stats"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -128,6 +138,45 @@ def ffs_sample_noalloc(U, dtype: int, L: int, N: int, B: int, seed: int, out_x, 
     _check(lib().ffs_sample_noalloc(_ptr(U), dtype, L, N, B, seed, _ptr(out_x), _stream(stream)))
 
 
+def ffs_sample_batched(handles, Bs, seeds, outs, stream=None):
+    """Sample many instances together (one grouped, graph-captured schedule)."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    b = (ctypes.c_int64 * n)(*Bs)
+    sd = (ctypes.c_uint64 * n)(*seeds)
+    o = (ctypes.c_void_p * n)(*[_ptr(x).value if x is not None else None for x in outs])
+    _check(lib().ffs_sample_batched(hs, b, sd, o, n, _stream(stream)), handles[0])
+
+
+def ffs_server_create(hbm_budget: int = 0, flags: int = 0, max_active: int = 0, stream=None):
+    s = ctypes.c_void_p()
+    _check(lib().ffs_server_create(hbm_budget, flags, max_active, _stream(stream), ctypes.byref(s)))
+    return s
+
+
+def ffs_submit(server, U, dtype: int, L: int, N: int, n_samples: int, seed: int, out_x) -> int:
+    rid = ctypes.c_uint64()
+    _check(lib().ffs_submit(server, _ptr(U), dtype, L, N, n_samples, seed, _ptr(out_x), ctypes.byref(rid)))
+    return rid.value
+
+
+def ffs_wait(server, req_id: int, timeout_ms: int = -1) -> float:
+    """Block until the request is done; returns its latency in ms (submission to completion)."""
+    lat = ctypes.c_double()
+    _check(lib().ffs_wait(server, req_id, timeout_ms, ctypes.byref(lat)))
+    return lat.value
+
+
+def ffs_server_stats(server):
+    p, a, it, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+    _check(lib().ffs_server_stats(server, ctypes.byref(p), ctypes.byref(a), ctypes.byref(it), ctypes.byref(b)))
+    return {"pending": p.value, "active": a.value, "iterations": it.value, "bytes_in_use": b.value}
+
+
+def ffs_server_destroy(server):
+    lib().ffs_server_destroy(server)
+
+
 def ffs_sync(h):
     _check(lib().ffs_sync(h), h)
 
@@ -177,6 +226,10 @@ class Sampler:
 
     def __init__(self, U, flags: int = 0, stream=None):
         self.L, self.N = int(U.shape[0]), int(U.shape[1])
+        if stream is not None and getattr(U, "is_cuda", False):
+            import torch
+
+            stream.wait_stream(torch.cuda.current_stream())  # U must be ready on the handle's stream
         self.h = ffs_create_ex(U, dtype_of(U), self.L, self.N, int(U.stride(0)) if hasattr(U, "stride")
                                else self.N, flags, stream)
 

@@ -173,3 +173,46 @@ def lattice_64x64_N1024(seed: int = 0):
 def anderson_L16384_N2048(seed: int = 0):
     """1D Anderson chain L = 16384, w_j ~ U[-1, 1], N = 2048, real."""
     return anderson_chain(16384, 2048, 1.0, seed)
+
+
+# ---------------------------------------------------------------------------------
+# Device-side generators for the large multi-instance workloads (seeded torch; the
+# QR / SVD are library factorisations, not sampling arithmetic).
+def haar_torch(L: int, N: int, seed: int, device="cuda", complex_=True):
+    """Haar-random L x N orbitals generated on the device: Q of the QR of a Gaussian."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    G = torch.randn((L, N), generator=g, device=device, dtype=torch.float64)
+    if complex_:
+        G = G + 1j * torch.randn((L, N), generator=g, device=device, dtype=torch.float64)
+    Q, _ = torch.linalg.qr(G)
+    return Q.contiguous()
+
+
+def lensemble_orbitals_torch(L: int, D: int, N: int, seed: int, device="cuda"):
+    """Top-N left singular vectors of L unit-norm Gaussian feature rows of dimension D."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    Phi = torch.randn((L, D), generator=g, device=device, dtype=torch.float64)
+    Phi = Phi / Phi.norm(dim=1, keepdim=True)
+    Uf, _, _ = torch.linalg.svd(Phi, full_matrices=False)
+    return Uf[:, :N].contiguous()
+
+
+def serving_requests(n: int, seed: int = 0, L_range=(500, 20000), D_range=(64, 512), N_max=200,
+                     samples=(1, 32)):
+    """Sizes of n serving requests: L log-uniform, D uniform, N uniform in [5, min(N_max, D)],
+    samples uniform; returns a list of (L, D, N, n_samples)."""
+    r = _rng(seed)
+    out = []
+    for _ in range(n):
+        L = int(round(math.exp(r.uniform(math.log(L_range[0]), math.log(L_range[1])))))
+        D = int(r.integers(D_range[0], D_range[1] + 1))
+        N = int(r.integers(5, min(N_max, D) + 1))
+        s = int(r.integers(samples[0], samples[1] + 1))
+        out.append((L, D, N, s))
+    return out
