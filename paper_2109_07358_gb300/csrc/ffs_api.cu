@@ -92,9 +92,9 @@ static size_t per_sample_bytes(const ffs_ctx* c) {
   b += (size_t)c->ldP * 4;                         // weights
   b += (size_t)c->N * c->N * state_elem_bytes(c);  // elimination state
   b += 8;                                          // logp
-  if (blocked(c)) {                                // saved panel vectors, couplings, pivots
+  if (blocked(c)) {                                // panel-start columns, panel inverse
     const size_t nb = blocked_panel_width();
-    b += ((size_t)c->N * nb + nb * nb + nb) * state_elem_bytes(c);
+    b += ((size_t)c->N * nb + nb * nb) * state_elem_bytes(c);
   }
   return b;
 }
@@ -105,13 +105,11 @@ static void free_workspace(ffs_ctx* c) {
   cudaFree(c->H);
   cudaFree(c->P);
   cudaFree(c->W);
-  cudaFree(c->WsT);
-  cudaFree(c->beta);
-  cudaFree(c->piv);
+  cudaFree(c->W0P);
+  cudaFree(c->Sinv);
   cudaFree(c->logp);
-  c->WsT = nullptr;
-  c->beta = nullptr;
-  c->piv = nullptr;
+  c->W0P = nullptr;
+  c->Sinv = nullptr;
   c->m = nullptr;
   c->mask = nullptr;
   c->H = nullptr;
@@ -134,9 +132,8 @@ static int ensure_workspace(ffs_ctx* c, int64_t Bw) {
   FFS_CUDA_TRY(c, cudaMalloc((void**)&c->logp, (size_t)Bw * 8));
   if (blocked(c)) {
     const size_t nb = blocked_panel_width(), es = state_elem_bytes(c);
-    FFS_CUDA_TRY(c, cudaMalloc(&c->WsT, (size_t)Bw * c->N * nb * es));
-    FFS_CUDA_TRY(c, cudaMalloc(&c->beta, (size_t)Bw * nb * nb * es));
-    FFS_CUDA_TRY(c, cudaMalloc(&c->piv, (size_t)Bw * nb * es));
+    FFS_CUDA_TRY(c, cudaMalloc(&c->W0P, (size_t)Bw * c->N * nb * es));
+    FFS_CUDA_TRY(c, cudaMalloc(&c->Sinv, (size_t)Bw * nb * nb * es));
   }
   c->ws_B = Bw;
   return FFS_OK;
@@ -433,9 +430,8 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
     BlockedArgs bt{};
     bt.Nc = n_steps;
     bt.W = h->W;
-    bt.WsT = h->WsT;
-    bt.beta = h->beta;
-    bt.piv = h->piv;
+    bt.W0P = h->W0P;
+    bt.Sinv = h->Sinv;
     if (!plain) FFS_CUDA_TRY(h, cudaMemsetAsync(h->H, 0, (size_t)h->ws_B * h->Kp * op_elem_bytes(op), st));
     FFS_CUDA_TRY(h, cudaMemsetAsync(h->mask, 0, (size_t)bw * h->ldMask * 4, st));
     FFS_CUDA_TRY(h, cudaMemsetAsync(h->logp, 0, (size_t)bw * 8, st));

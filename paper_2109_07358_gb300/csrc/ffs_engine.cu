@@ -68,9 +68,8 @@ void fill_inst(GroupInst& g, ffs_ctx* c, int64_t B, uint64_t seed, uint64_t firs
   BlockedArgs& t = g.t;
   t.Nc = n_steps;
   t.W = c->W;
-  t.WsT = c->WsT;
-  t.beta = c->beta;
-  t.piv = c->piv;
+  t.W0P = c->W0P;
+  t.Sinv = c->Sinv;
   TcArgs& p = g.tc;
   p.bw = B;
   p.L = c->L;
@@ -85,7 +84,7 @@ void fill_inst(GroupInst& g, ffs_ctx* c, int64_t B, uint64_t seed, uint64_t firs
   g.n_btiles = (B + 127) / 128;
 }
 
-enum LaunchKind { kInit = 0, kResidual = 1, kStep = 2, kPanelUpd = 3 };
+enum LaunchKind { kInit = 0, kResidual = 1, kStep = 2, kPanelS = 3, kPanelUpd = 4 };
 
 struct Launch {
   int kind;
@@ -113,10 +112,19 @@ struct LaunchBuilder {
   }
 };
 
-int64_t panel_items(int64_t B, int64_t k, int64_t Nc) {
+bool panel_end(int64_t k, int64_t Nc) {
   const int64_t k1 = std::min((k / kPanel) * kPanel + kPanel, Nc);
-  if (k + 1 != k1 || k1 >= Nc) return 0;  // not the last step of a panel, or the last panel
+  return k + 1 == k1 && k1 < Nc;  // last step of a panel that has trailing columns
+}
+int64_t panel_items(int64_t B, int64_t k, int64_t Nc) {
+  if (!panel_end(k, Nc)) return 0;
+  const int64_t k1 = k + 1;
   return B * ((Nc - k1 + 31) / 32);
+}
+int64_t panel_s_items(int64_t B, int64_t k, int64_t Nc) { return panel_end(k, Nc) ? B : 0; }
+int64_t step_items(int64_t B) {
+  const int64_t w = blocked_step_samples_per_cta();
+  return (B + w - 1) / w;
 }
 
 cudaError_t issue(const Launch& L, const GroupInst* d_inst, const GroupEntry* d_ent, bool cplx, int state, int op,
@@ -126,6 +134,7 @@ cudaError_t issue(const Launch& L, const GroupInst* d_inst, const GroupEntry* d_
     case kInit: return launch_group_init(d_inst, e, L.n, L.total, op, s);
     case kResidual: return launch_group_residual(d_inst, e, L.n, L.total, op, s);
     case kStep: return launch_group_step(d_inst, e, L.n, L.total, cplx, state, op, maxNc, s);
+    case kPanelS: return launch_group_panel_s(d_inst, e, L.n, L.total, cplx, state, s);
     case kPanelUpd: return launch_group_panel(d_inst, e, L.n, L.total, cplx, state, op, s);
   }
   return cudaErrorInvalidValue;
@@ -199,8 +208,12 @@ extern "C" int ffs_sample_batched(ffs_handle* hs, const int64_t* Bs, const uint6
     res.done();
     LaunchBuilder stp(ents, launches, kStep);
     for (int i = 0; i < ni; ++i)
-      if (k < Ns[i]) stp.add(i, k, Bv[i]);
+      if (k < Ns[i]) stp.add(i, k, step_items(Bv[i]));
     stp.done();
+    LaunchBuilder pas(ents, launches, kPanelS);
+    for (int i = 0; i < ni; ++i)
+      if (k < Ns[i]) pas.add(i, k, panel_s_items(Bv[i], k, Ns[i]));
+    pas.done();
     LaunchBuilder pan(ents, launches, kPanelUpd);
     for (int i = 0; i < ni; ++i)
       if (k < Ns[i]) pan.add(i, k, panel_items(Bv[i], k, Ns[i]));
@@ -410,8 +423,11 @@ void engine_loop(ffs_server* s) {
         for (int i = 0; i < ni; ++i) res.add(i, members[i]->k, inst[i].n_btiles * inst[i].n_jtiles);
         res.done();
         LaunchBuilder stp(ents, launches, kStep);
-        for (int i = 0; i < ni; ++i) stp.add(i, members[i]->k, members[i]->n);
+        for (int i = 0; i < ni; ++i) stp.add(i, members[i]->k, step_items(members[i]->n));
         stp.done();
+        LaunchBuilder pas(ents, launches, kPanelS);
+        for (int i = 0; i < ni; ++i) pas.add(i, members[i]->k, panel_s_items(members[i]->n, members[i]->k, members[i]->N));
+        pas.done();
         LaunchBuilder pan(ents, launches, kPanelUpd);
         for (int i = 0; i < ni; ++i) pan.add(i, members[i]->k, panel_items(members[i]->n, members[i]->k, members[i]->N));
         pan.done();

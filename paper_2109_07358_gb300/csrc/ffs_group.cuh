@@ -35,14 +35,16 @@ __device__ __forceinline__ int group_find(const GroupEntry* __restrict__ e, int 
   return lo;
 }
 
-// Items per instance: init ceil(bw/128) CTAs; residual n_btiles*n_jtiles; step bw;
-// panel bw * ceil((Nc - k1)/32).
+// Items per instance: init ceil(bw/128) CTAs; residual n_btiles*n_jtiles; step
+// ceil(bw/8) (a warp per sample); panel S bw; panel bw * ceil((Nc - k1)/32).
 cudaError_t launch_group_init(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op,
                               cudaStream_t s);
 cudaError_t launch_group_residual(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op,
                                   cudaStream_t s);
 cudaError_t launch_group_step(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, bool cplx,
                               int state, int op, int64_t maxNc, cudaStream_t s);
+cudaError_t launch_group_panel_s(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, bool cplx,
+                                 int state, cudaStream_t s);
 cudaError_t launch_group_panel(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, bool cplx,
                                int state, int op, cudaStream_t s);
 cudaError_t configure_group();

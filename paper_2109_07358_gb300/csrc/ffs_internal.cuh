@@ -163,9 +163,8 @@ struct ffs_ctx {
   void* H = nullptr;             // Bw x Kp residual operand (per-mode element type / planes)
   float* P = nullptr;            // Bw x ldP masked weights |u_y^T h|^2 of the current step
   void* W = nullptr;             // Bw x N x N elimination state (state precision)
-  void* WsT = nullptr;           // Bw x N x 32 saved normal vectors of the current panel
-  void* beta = nullptr;          // Bw x 32 x 32 panel couplings
-  void* piv = nullptr;           // Bw x 32 panel pivots
+  void* W0P = nullptr;           // Bw x N x 32 old rows' panel columns at the panel start
+  void* Sinv = nullptr;          // Bw x 32 x 32 inverse of the panel Schur complement
   double* logp = nullptr;        // Bw
   int32_t* xbuf = nullptr;       // Bw x n_steps when the caller's buffer is on the host
   int32_t* fbuf = nullptr;       // Bw x n_steps teacher-forcing copy

@@ -38,13 +38,13 @@ struct StepArgs {
 // Precision of the per-sample elimination state.
 enum StateKind : int { kStateFP64 = 0, kStateFP32 = 1, kStateDF64 = 2 };
 
-// Buffers of the blocked state (per sample: W N x N, WsT N x 32, beta 32 x 32, piv 32).
+// Buffers of the blocked state (per sample: W N x N, W0P N x 32 panel-start copy of the
+// old rows' panel columns, Sinv 32 x 32 inverse of the panel Schur complement).
 struct BlockedArgs {
   int64_t Nc;  // state columns kept (= steps taken)
   void* W;
-  void* WsT;
-  void* beta;
-  void* piv;
+  void* W0P;
+  void* Sinv;
 };
 
 cudaError_t launch_blocked_step(const StepArgs& a, const BlockedArgs& t, int64_t k, int state, int op,
@@ -54,6 +54,7 @@ cudaError_t launch_blocked_panel(const StepArgs& a, const BlockedArgs& t, int64_
 size_t blocked_elem_bytes(bool cplx, int state);
 size_t blocked_step_smem(int64_t Nc, bool cplx, int state);
 int blocked_panel_width();
+int blocked_step_samples_per_cta();
 cudaError_t configure_blocked();
 
 cudaError_t launch_perm_init(const StepArgs& a, int op_mode, cudaStream_t s);

@@ -6,20 +6,21 @@
 // here the base rows are also reduced against each other, so that the next normal
 // vector is simply h_{k+1} = (-W[:, k+1] ; 1) in the sample's column order).
 //
-// Updating all N-k future columns at every step costs a pass over the whole state per
-// step.  Instead the columns are processed in panels of NB = 32:
-//   per step (tail_step_kernel): draw x_k; reduce the new row u = U[x_k, m] against the
-//     state only on the remaining panel columns [k, k1); pivot s_k = the reduced value at
-//     column k (the Schur residual of x_k); rank-1 update of the panel columns; save w_k
-//     (the old column k, i.e. the current normal vector) and the couplings
-//     beta[k][k'] = u_k' - u_<k' . w_k' for the earlier panel steps k'.
-//   per panel (tail_panel_kernel), for the trailing columns T = [k1, Nc):
-//     Y   = U[x_new, m_T] - U[x_new, m_<k0] W0_T            (GEMM, nb x k0 x |T|)
-//     n_i = (Y_i - sum_{i'<i} beta[i][i'] n_i') / s_i       (forward substitution)
-//     W[old rows, T] = W0_T - Wsave_old n                    (GEMM, k0 x nb x |T|)
-//     W[new row j, T] = n_j - sum_{i>j} w_{k0+i}[k0+j] n_i
-//   which is exactly the sequence of per-step updates the unblocked form would apply
-//   to T, regrouped.  The state therefore stays identical in exact arithmetic.
+// Updating all remaining columns at every step would stream the whole state once per
+// step.  The columns are instead processed in panels P = [k0, k1) of 32:
+//   per step (tail_step_kernel, one warp per sample): draw x_k; reduce the new row
+//     u = U[x_k, m] against the state on the panel columns [k, k1) only (lane = column);
+//     pivot s_k = the reduced value at column k (the Schur residual of x_k); rank-1
+//     update of the panel columns; the first step of a panel keeps a copy W0_P of the
+//     old rows' panel columns.
+//   per panel, for the trailing columns T = [k1, Nc), by the block-inverse identity:
+//     S   = U[x_new, m_P] - U[x_new, m_<k0] W0_P            (panel Schur complement)
+//     Y   = U[x_new, m_T] - U[x_new, m_<k0] W0_T
+//     Bot = S^-1 Y                                          (new rows)
+//     Top = W0_T - W0_P Bot                                 (old rows)
+//   tail_panel_s_kernel forms S and inverts it (Gauss-Jordan, pivots in draw order, as
+//   the per-step updates do); tail_panel_kernel applies the two GEMM-shaped updates.
+//   In exact arithmetic this is the same state the per-step updates would produce.
 // Only the first Nc = n_steps columns are kept (marginal sampling needs no more).
 #include <type_traits>
 
@@ -30,7 +31,8 @@
 
 namespace fermi {
 
-constexpr int NB = 32;  // panel width (== warp size: one lane per panel column)
+constexpr int NB = 32;           // panel width (== warp size: one lane per panel column)
+constexpr int kStepWarps = 8;    // samples per CTA of the step kernel
 
 __device__ __forceinline__ void put_out(const StepArgs& a, int op, int64_t b, int col, double v) {
   const size_t idx = (size_t)b * a.Kp + col;
@@ -59,114 +61,341 @@ __device__ __forceinline__ void put_h(const StepArgs& a, int op, int64_t b, int 
   put_out(a, op, b, 2 * col, v.re);
   put_out(a, op, b, 2 * col + 1, v.im);
 }
+// Double-float value straight to the operand encoding, on the FP32 pipes: the BF16 low
+// part is the rounded remainder (hi_f - hi_bf16) + lo_f, whose FP32 rounding is far below
+// a BF16 ulp of the low part.
+__device__ __forceinline__ void put_out_df(const StepArgs& a, int op, int64_t b, int col, df v) {
+  const size_t idx = (size_t)b * a.Kp + col;
+  switch (op) {
+    case kOpF32: ((float*)a.H)[idx] = __fadd_rn(v.hi, v.lo); break;
+    case kOpTF32: {
+      uint32_t r;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(__fadd_rn(v.hi, v.lo)));
+      ((float*)a.H)[idx] = __uint_as_float(r);
+      break;
+    }
+    case kOpBF16x3: {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v.hi);
+      ((__nv_bfloat16*)a.H)[idx] = hi;
+      ((__nv_bfloat16*)a.H)[a.hplane + idx] =
+          __float2bfloat16_rn(__fadd_rn(__fsub_rn(v.hi, __bfloat162float(hi)), v.lo));
+      break;
+    }
+    case kOpBF16: ((__nv_bfloat16*)a.H)[idx] = __float2bfloat16_rn(v.hi); break;
+    default: break;
+  }
+}
+template <typename A> __device__ __forceinline__ void put_state(const StepArgs& a, int op, int64_t b, int col, A v) {
+  if constexpr (std::is_same<A, df>::value) {
+    put_out_df(a, op, b, col, v);
+  } else if constexpr (std::is_same<A, cdf>::value) {
+    put_out_df(a, op, b, 2 * col, v.re);
+    put_out_df(a, op, b, 2 * col + 1, v.im);
+  } else {
+    put_h(a, op, b, col, Ar<A>::out(v));
+  }
+}
 
-// Step k of sample b of one instance, executed by one 256-thread CTA.
+template <typename A> __device__ __forceinline__ A shfl_idx_any(A v, int src) {
+  constexpr int Wd = sizeof(A) / 4;
+  uint32_t w[Wd];
+  memcpy(w, &v, sizeof(A));
+#pragma unroll
+  for (int q = 0; q < Wd; ++q) w[q] = __shfl_sync(0xffffffffu, w[q], src);
+  memcpy(&v, w, sizeof(A));
+  return v;
+}
+
+// ------------------------------------------------------------------ warp draw
+// Sum of the 128 weights of chunk ch (each lane loads 4), identical in every lane.
+__device__ __forceinline__ double chunk_sum(const float* __restrict__ p, int64_t L, int64_t ch, int lane) {
+  const int64_t y0 = ch * 128 + 4 * lane;
+  float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+  if (y0 + 3 < L) {
+    const float4 v = *(const float4*)(p + y0);
+    v0 = v.x, v1 = v.y, v2 = v.z, v3 = v.w;
+  } else {
+    if (y0 < L) v0 = p[y0];
+    if (y0 + 1 < L) v1 = p[y0 + 1];
+    if (y0 + 2 < L) v2 = p[y0 + 2];
+  }
+  float s = (v0 + v1) + (v2 + v3);
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return (double)s;
+}
+
+// First site of chunk ch with a nonzero weight whose running sum, started at base,
+// exceeds t; -1 when rounding leaves none in the chunk.
+__device__ __forceinline__ int chunk_find(const float* __restrict__ p, int64_t L, int64_t ch, int lane, double base,
+                                          double t) {
+  const int64_t y0 = ch * 128 + 4 * lane;
+  float w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) w[q] = (y0 + q < L) ? p[y0 + q] : 0.f;
+  float run[4];
+  float acc = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    acc += w[q];
+    run[q] = acc;
+  }
+  float incl = acc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const float v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  // running sums within the chunk in FP32 (128 terms), the chunk base in FP64
+  const float excl = incl - acc;
+  const float tl = (float)(t - base);
+  int q_hit = -1;
+#pragma unroll
+  for (int q = 3; q >= 0; --q)
+    if (w[q] > 0.f && excl + run[q] > tl) q_hit = q;
+  const unsigned hit = __ballot_sync(0xffffffffu, q_hit >= 0);
+  if (!hit) return -1;
+  const int src = __ffs(hit) - 1;
+  const int qs = __shfl_sync(0xffffffffu, q_hit, src);
+  return (int)(ch * 128 + 4 * src + qs);
+}
+
+__device__ __forceinline__ int last_nonzero(const float* __restrict__ p, int64_t L, int lane) {
+  int last = -1;
+  for (int64_t y = lane; y < L; y += 32)
+    if (p[y] > 0.f) last = (int)y;
+  for (int o = 16; o; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
+  return last;
+}
+
+// ------------------------------------------------------------------ per-step body (one warp)
 template <typename A>
-__device__ __forceinline__ void step_body(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k,
-                                          int op_mode, unsigned char* smem_raw, DrawShared& dsh) {
+__device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k,
+                                          int op_mode) {
   using T = Ar<A>;
   using U = typename T::U;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t N = a.N, Nc = t.Nc;
+  const int lane = threadIdx.x & 31;
+  const int64_t L = a.L, N = a.N, Nc = t.Nc;
   const float* __restrict__ prow = a.P + b * a.ldP;
 
+  // draw: Z over 128-site chunks, then the first chunk whose running sum passes t
+  const int64_t nch = (L + 127) / 128;
   double Z = 0.0;
-  const int x = block_draw(prow, a.L, a.seed, a.first + (uint64_t)b, k, forced_site(a, b, k), a.status, dsh, Z);
-  draw_outputs(a, b, k, x, Z, prow);
+  for (int64_t ch = 0; ch < nch; ++ch) Z += chunk_sum(prow, L, ch, lane);
+  int x;
+  const int f = forced_site(a, b, k);
+  if (f != -1) {
+    if (f == -2 && lane == 0) set_status(a.status, FFS_E_ARG);
+    x = f < 0 ? 0 : f;
+  } else {
+    const double tt = site_uniform(a.seed, a.first + (uint64_t)b, (int)k) * Z;
+    x = -1;
+    double base = 0.0;
+    for (int64_t ch = 0; ch < nch && x < 0; ++ch) {
+      const double cs = chunk_sum(prow, L, ch, lane);
+      if (base + cs > tt) x = chunk_find(prow, L, ch, lane, base, tt);
+      base += cs;
+    }
+    if (x < 0) x = last_nonzero(prow, L, lane);
+    if (x < 0) {
+      if (lane == 0) set_status(a.status, FFS_E_NUMERIC);
+      x = 0;
+    }
+  }
+  if (lane == 0) {
+    a.x[b * a.n_steps + k] = x;
+    a.mask[b * a.ldMask + (x >> 5)] |= 1u << (x & 31);
+    const double px = (double)prow[x];
+    a.logp[b] += (px > 0.0 && Z > 0.0) ? log(px / Z) : -INFINITY;
+    if (!(Z > 0.0) || !isfinite(Z)) set_status(a.status, FFS_E_NUMERIC);
+  }
+  if (a.probs) {
+    float* pr = a.probs + ((size_t)b * a.n_steps + k) * L;
+    const double iz = Z > 0.0 ? 1.0 / Z : 0.0;
+    for (int64_t y = lane; y < L; y += 32) pr[y] = (float)((double)prow[y] * iz);
+  }
   if (k + 1 >= a.n_steps) return;
 
   const int64_t k0 = (k / NB) * NB, i = k - k0, k1 = min(k0 + NB, Nc);
   A* W = (A*)t.W + (size_t)b * N * N;
-  A* WsT = (A*)t.WsT + (size_t)b * N * NB;
-  A* beta = (A*)t.beta + (size_t)b * NB * NB;
-  A* piv = (A*)t.piv + (size_t)b * NB;
-  A* r = (A*)smem_raw;
-  A* wk = r + Nc;
-  A* red = wk + Nc;  // 8 x 32 partial sums
-  A* nv = red + 8 * 32;
-  int* ms = (int*)(nv + 32);
+  A* W0P = (A*)t.W0P + (size_t)b * N * NB;
   const int32_t* mrow = a.m + b * N;
   const U* urow = (const U*)a.U64 + (int64_t)x * N;
-  for (int64_t c = tid; c < Nc; c += blockDim.x) {
-    const int mc = mrow[c];
-    ms[c] = mc;
-    r[c] = T::from(urow[mc]);
-  }
-  for (int64_t j = tid; j < k; j += blockDim.x) {
-    const A w = W[j * N + k];
-    wk[j] = w;
-    WsT[j * NB + i] = w;
-  }
-  __syncthreads();
-
-  // couplings with the earlier steps of this panel: beta[i][i'] = u_k' - u_<k' . w_k'
-  for (int64_t ip = warp; ip < i; ip += 8) {
-    const int64_t kp = k0 + ip;
-    A acc = T::zero();
-    for (int64_t j = lane; j < kp; j += 32) acc = T::fms(acc, r[j], WsT[j * NB + ip]);
-    for (int o = 16; o; o >>= 1) acc = T::add(acc, shfl_xor_any(acc, o));
-    if (lane == 0) beta[i * NB + ip] = T::add(r[kp], acc);
-  }
-
-  // reduce the new row on the panel columns [k, k1): lane = column, warp = row group
   const int64_t c = k + lane;
   const bool cval = c < k1;
-  A part = T::zero();
-  if (cval)
-    for (int64_t j = warp; j < k; j += 8) part = T::fms(part, r[j], W[j * N + c]);
-  red[warp * 32 + lane] = part;
-  __syncthreads();
-  if (warp == 0 && cval) {
-    A s = r[c];
-    for (int w = 0; w < 8; ++w) s = T::add(s, red[w * 32 + lane]);
-    nv[lane] = s;
+
+  // first step of a panel: keep the old rows' panel columns for the panel-end update
+  if (i == 0 && k0 > 0 && lane < k1 - k0)
+    for (int64_t j = 0; j < k0; ++j) W0P[j * NB + lane] = W[j * N + k0 + lane];
+
+  // reduce the new row on the panel columns: r'[c] = u[c] - sum_{j<k} u[j] W[j][c]
+  // (rows in groups of 8 whose loads are issued together; two accumulation chains)
+  A acc = T::zero(), acc2 = T::zero();
+  for (int64_t j0 = 0; j0 < k; j0 += 32) {
+    const int64_t jl = j0 + lane;
+    const A uj = (jl < k) ? T::from(urow[mrow[jl]]) : T::zero();
+    const int jn = (int)min((int64_t)32, k - j0);
+    int jj = 0;
+    for (; jj + 8 <= jn; jj += 8) {
+      A wv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) wv[q] = cval ? W[(j0 + jj + q) * N + c] : T::zero();
+#pragma unroll
+      for (int q = 0; q < 8; q += 2) {
+        acc = T::fms(acc, shfl_idx_any(uj, jj + q), wv[q]);
+        acc2 = T::fms(acc2, shfl_idx_any(uj, jj + q + 1), wv[q + 1]);
+      }
+    }
+    for (; jj < jn; ++jj) {
+      const A u = shfl_idx_any(uj, jj);
+      if (cval) acc = T::fms(acc, u, W[(j0 + jj) * N + c]);
+    }
   }
-  __syncthreads();
-  const A s = nv[0];  // pivot: the Schur residual of x_k
-  if (tid == 0) {
-    piv[i] = s;
+  acc = T::add(acc, acc2);
+  const A rc = cval ? T::add(T::from(urow[mrow[c]]), acc) : T::zero();
+  const A s = shfl_idx_any(rc, 0);  // pivot: the Schur residual of x_k
+  if (lane == 0) {
     const double s2 = T::abs2(s);
     if (!(s2 > 1e-300) || !isfinite(s2)) set_status(a.status, FFS_E_NUMERIC);
   }
-  __syncthreads();
-  if (warp == 0 && cval && lane > 0) nv[lane] = T::div(nv[lane], s);
-  __syncthreads();
-  if (cval && lane > 0) {
-    const A ncv = nv[lane];
-    for (int64_t j = warp; j < k; j += 8) W[j * N + c] = T::fms(W[j * N + c], wk[j], ncv);
-    if (warp == 0) W[k * N + c] = ncv;
+  const bool upd = cval && lane > 0;
+  const A ncv = upd ? T::div(rc, s) : T::zero();
+
+  // rank-1 update of the panel columns (k, k1) with the old column k; then the new row
+  for (int64_t j0 = 0; j0 < k; j0 += 32) {
+    const int64_t jl = j0 + lane;
+    const A wj = (jl < k) ? W[jl * N + k] : T::zero();
+    const int jn = (int)min((int64_t)32, k - j0);
+    int jj = 0;
+    for (; jj + 8 <= jn; jj += 8) {
+      A wv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) wv[q] = upd ? W[(j0 + jj + q) * N + c] : T::zero();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const A w = shfl_idx_any(wj, jj + q);
+        if (upd) W[(j0 + jj + q) * N + c] = T::fms(wv[q], w, ncv);
+      }
+    }
+    for (; jj < jn; ++jj) {
+      const A w = shfl_idx_any(wj, jj);
+      if (upd) {
+        A* p = W + (j0 + jj) * N + c;
+        *p = T::fms(*p, w, ncv);
+      }
+    }
   }
-  __syncthreads();
+  if (upd) W[k * N + c] = ncv;
+  __syncwarp();
 
   // operand of step k+1 while column k+1 is still inside this panel
   if (op_mode != kOpNone && k + 1 < k1) {
-    for (int64_t j = tid; j <= k + 1; j += blockDim.x) {
+    for (int64_t j = lane; j <= k + 1; j += 32) {
       const A v = (j <= k) ? T::neg(W[j * N + k + 1]) : T::one();
-      put_h(a, op_mode, b, ms[j], T::out(v));
+      put_state<A>(a, op_mode, b, mrow[j], v);
     }
   }
 }
 
 template <typename A>
 __global__ void __launch_bounds__(256) tail_step_kernel(StepArgs a, BlockedArgs t, int64_t k, int op_mode) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ DrawShared dsh;
-  step_body<A>(a, t, blockIdx.x, k, op_mode, smem_raw, dsh);
+  const int64_t b = (int64_t)blockIdx.x * kStepWarps + (threadIdx.x >> 5);
+  if (b >= a.bw) return;
+  step_warp<A>(a, t, b, k, op_mode);
 }
 
-// Trailing update of sample b on the 32 columns cb of T = [k1, Nc), one 256-thread CTA.
+// ------------------------------------------------------------------ panel end: S^-1
+// S = U[x_new, m_P] - U[x_new, m_<k0] W0_P, inverted in shared memory (one CTA per sample).
+template <typename A>
+__device__ __forceinline__ void panel_s_body(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k0,
+                                             int64_t k1, unsigned char* smem_raw) {
+  using T = Ar<A>;
+  using U = typename T::U;
+  A* Aug = (A*)smem_raw;        // NB x 2NB: [S | I] -> [I | S^-1]
+  A* Cs = Aug + NB * 2 * NB;    // NB x 32 chunk of U[x_new, m_j]
+  A* Ws = Cs + NB * 32;         // 32 x NB chunk of W0_P
+  A* fac = Ws + 32 * NB;        // NB elimination factors, then the pivot
+  int* xs = (int*)(fac + NB + 1);
+  int* mj = xs + NB;
+  const int tid = threadIdx.x;
+  const int64_t N = a.N;
+  const int nbr = (int)(k1 - k0);
+  const int32_t* mrow = a.m + b * N;
+  const U* U64 = (const U*)a.U64;
+  const A* W0P = (const A*)t.W0P + (size_t)b * N * NB;
+  if (tid < NB) xs[tid] = tid < nbr ? a.x[b * a.n_steps + k0 + tid] : 0;
+  __syncthreads();
+  // thread owns entries (ii, cc) = (tid / 32 + 8 q, tid % 32)
+  const int cc = tid & 31, r0 = tid >> 5;
+  A acc[NB / 8];
+#pragma unroll
+  for (int q = 0; q < NB / 8; ++q) {
+    const int ii = r0 + 8 * q;
+    acc[q] = (ii < nbr && cc < nbr) ? T::from(U64[(int64_t)xs[ii] * N + mrow[k0 + cc]]) : T::zero();
+  }
+  for (int64_t j0 = 0; j0 < k0; j0 += 32) {
+    if (tid < 32) mj[tid] = (j0 + tid < k0) ? mrow[j0 + tid] : 0;
+    __syncthreads();
+    for (int e = tid; e < NB * 32; e += blockDim.x) {
+      const int ii = e >> 5, jj = e & 31;
+      Cs[e] = (ii < nbr && j0 + jj < k0) ? T::from(U64[(int64_t)xs[ii] * N + mj[jj]]) : T::zero();
+      Ws[e] = (j0 + ii < k0 && jj < nbr) ? W0P[(j0 + ii) * NB + jj] : T::zero();  // row ii of the chunk
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < 32; ++jj) {
+      const A w = Ws[jj * NB + cc];
+#pragma unroll
+      for (int q = 0; q < NB / 8; ++q) acc[q] = T::fms(acc[q], Cs[(r0 + 8 * q) * 32 + jj], w);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < NB / 8; ++q) {
+    const int ii = r0 + 8 * q;
+    Aug[ii * 2 * NB + cc] = acc[q];
+    Aug[ii * 2 * NB + NB + cc] = (ii == cc) ? T::one() : T::zero();
+  }
+  __syncthreads();
+  // Gauss-Jordan without pivot search: the pivots are taken in draw order
+  for (int p = 0; p < nbr; ++p) {
+    if (tid == 0) {
+      fac[NB] = Aug[p * 2 * NB + p];
+      const double p2 = T::abs2(fac[NB]);
+      if (!(p2 > 1e-300) || !isfinite(p2)) set_status(a.status, FFS_E_NUMERIC);
+    }
+    __syncthreads();
+    if (tid < 2 * NB) Aug[p * 2 * NB + tid] = T::div(Aug[p * 2 * NB + tid], fac[NB]);
+    if (tid < NB) fac[tid] = Aug[tid * 2 * NB + p];
+    __syncthreads();
+    for (int e = tid; e < NB * 2 * NB; e += blockDim.x) {
+      const int rr = e / (2 * NB), col = e % (2 * NB);
+      if (rr != p && rr < nbr) Aug[e] = T::fms(Aug[e], fac[rr], Aug[p * 2 * NB + col]);
+    }
+    __syncthreads();
+  }
+  A* Sinv = (A*)t.Sinv + (size_t)b * NB * NB;
+  for (int e = tid; e < NB * NB; e += blockDim.x) Sinv[e] = Aug[(e / NB) * 2 * NB + NB + (e % NB)];
+}
+
+template <typename A>
+__global__ void __launch_bounds__(256) tail_panel_s_kernel(StepArgs a, BlockedArgs t, int64_t k0, int64_t k1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  panel_s_body<A>(a, t, blockIdx.x, k0, k1, smem_raw);
+}
+
+// ------------------------------------------------------------------ panel end: trailing columns
+// Sample b, columns [k1 + 32 cb, +32) of T: Y, Bot = S^-1 Y, Top = W0_T - W0_P Bot.
 template <typename A>
 __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t cb,
                                            int64_t k0, int64_t k1, int op_mode, unsigned char* smem_raw) {
   using T = Ar<A>;
   using U = typename T::U;
-  A* Ys = (A*)smem_raw;         // NB x 32: Y, then n
-  A* Cs = Ys + NB * 32;         // NB x 32: U[x_new, m_j] chunk
-  A* Ws = Cs + NB * 32;         // 32 x 32: W chunk
-  A* bs = Ws + 32 * 32;         // NB x NB couplings
-  A* ps = bs + NB * NB;         // NB pivots
-  int* xs = (int*)(ps + NB);    // NB new sites
-  int* mj = xs + NB;            // 32: m of the current K chunk
+  A* Ys = (A*)smem_raw;     // NB x 32: Y
+  A* Bs = Ys + NB * 32;     // NB x 32: Bot
+  A* Cs = Bs + NB * 32;     // NB x 32: U[x_new, m_j] chunk
+  A* Ws = Cs + NB * 32;     // 32 x 32: W0_T chunk
+  A* Si = Ws + 32 * 32;     // NB x NB: S^-1
+  int* xs = (int*)(Si + NB * NB);
+  int* mj = xs + NB;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t N = a.N, Nc = t.Nc;
   const int nbr = (int)(k1 - k0);
@@ -174,15 +403,12 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   const int64_t c = c0 + lane;
   const bool cval = c < Nc;
   A* W = (A*)t.W + (size_t)b * N * N;
-  const A* WsT = (const A*)t.WsT + (size_t)b * N * NB;
+  const A* W0P = (const A*)t.W0P + (size_t)b * N * NB;
   const int32_t* mrow = a.m + b * N;
   const U* U64 = (const U*)a.U64;
 
-  for (int e = tid; e < NB * NB; e += blockDim.x) bs[e] = ((const A*)t.beta)[(size_t)b * NB * NB + e];
-  if (tid < NB) {
-    ps[tid] = ((const A*)t.piv)[(size_t)b * NB + tid];
-    xs[tid] = tid < nbr ? a.x[b * a.n_steps + k0 + tid] : 0;
-  }
+  for (int e = tid; e < NB * NB; e += blockDim.x) Si[e] = ((const A*)t.Sinv)[(size_t)b * NB * NB + e];
+  if (tid < NB) xs[tid] = tid < nbr ? a.x[b * a.n_steps + k0 + tid] : 0;
   __syncthreads();
 
   // Y = U[x_new, m_T] - U[x_new, m_<k0] W0_T; thread owns rows warp + 8q, column lane
@@ -193,55 +419,139 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
     const int ii = warp + 8 * q;
     acc[q] = (ii < nbr && cval) ? T::from(U64[(int64_t)xs[ii] * N + mc]) : T::zero();
   }
-  for (int64_t j0 = 0; j0 < k0; j0 += 32) {
-    if (tid < 32) mj[tid] = (j0 + tid < k0) ? mrow[j0 + tid] : 0;
-    __syncthreads();
-    for (int e = tid; e < NB * 32; e += blockDim.x) {
-      const int ii = e >> 5, jj = e & 31;
-      Cs[e] = (ii < nbr && j0 + jj < k0) ? T::from(U64[(int64_t)xs[ii] * N + mj[jj]]) : T::zero();
-    }
-    for (int e = tid; e < 32 * 32; e += blockDim.x) {
-      const int jj = e >> 5, cc = e & 31;
-      Ws[e] = (j0 + jj < k0 && c0 + cc < Nc) ? W[(j0 + jj) * N + c0 + cc] : T::zero();
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int jj = 0; jj < 32; ++jj) {
-      const A w = Ws[jj * 32 + lane];
+  if constexpr (std::is_same<A, cdf>::value || std::is_same<A, df>::value) {
+    // double-float: lazily renormalised accumulators; complex products by Karatsuba
+    // (re = S1 - S2, im = S3 - S1 - S2 with S1 = sum c.re w.re, S2 = sum c.im w.im,
+    // S3 = sum (c.re + c.im)(w.re + w.im)): three real products instead of four.
+    constexpr bool CX = std::is_same<A, cdf>::value;
+    df* Csum = (df*)(mj + 32);  // after the index arrays (16-byte aligned)
+    df* Wsum = Csum + NB * 32;
+    lzf S1[NB / 8], S2[NB / 8], S3[NB / 8];
 #pragma unroll
-      for (int q = 0; q < NB / 8; ++q) acc[q] = T::fms(acc[q], Cs[(warp + 8 * q) * 32 + jj], w);
+    for (int q = 0; q < NB / 8; ++q) S1[q] = S2[q] = S3[q] = lzf{0.f, 0.f};
+    for (int64_t j0 = 0; j0 < k0; j0 += 32) {
+      if (tid < 32) mj[tid] = (j0 + tid < k0) ? mrow[j0 + tid] : 0;
+      __syncthreads();
+      for (int e = tid; e < NB * 32; e += blockDim.x) {
+        const int ii = e >> 5, jj = e & 31;
+        const A v = (ii < nbr && j0 + jj < k0) ? T::from(U64[(int64_t)xs[ii] * N + mj[jj]]) : T::zero();
+        Cs[e] = v;
+        if constexpr (CX) Csum[e] = df_add(v.re, v.im);
+      }
+      for (int e = tid; e < 32 * 32; e += blockDim.x) {
+        const int jj = e >> 5, cc = e & 31;
+        const A v = (j0 + jj < k0 && c0 + cc < Nc) ? W[(j0 + jj) * N + c0 + cc] : T::zero();
+        Ws[e] = v;
+        if constexpr (CX) Wsum[e] = df_add(v.re, v.im);
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int jj = 0; jj < 32; ++jj) {
+        const A w = Ws[jj * 32 + lane];
+        if constexpr (CX) {
+          const df wsum = Wsum[jj * 32 + lane];
+#pragma unroll
+          for (int q = 0; q < NB / 8; ++q) {
+            const int ci = (warp + 8 * q) * 32 + jj;
+            const A cv = Cs[ci];
+            lz_mac(S1[q], cv.re, w.re);
+            lz_mac(S2[q], cv.im, w.im);
+            lz_mac(S3[q], Csum[ci], wsum);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < NB / 8; ++q) lz_mac(S1[q], Cs[(warp + 8 * q) * 32 + jj], w);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NB / 8; ++q) {
+      if constexpr (CX) {
+        const df p1 = lz_get(S1[q]), p2 = lz_get(S2[q]), p3 = lz_get(S3[q]);
+        const df re = df_sub(p1, p2), im = df_sub(df_sub(p3, p1), p2);
+        acc[q] = A{df_sub(acc[q].re, re), df_sub(acc[q].im, im)};
+      } else {
+        acc[q] = df_sub(acc[q], lz_get(S1[q]));
+      }
+    }
+  } else {
+    for (int64_t j0 = 0; j0 < k0; j0 += 32) {
+      if (tid < 32) mj[tid] = (j0 + tid < k0) ? mrow[j0 + tid] : 0;
+      __syncthreads();
+      for (int e = tid; e < NB * 32; e += blockDim.x) {
+        const int ii = e >> 5, jj = e & 31;
+        Cs[e] = (ii < nbr && j0 + jj < k0) ? T::from(U64[(int64_t)xs[ii] * N + mj[jj]]) : T::zero();
+      }
+      for (int e = tid; e < 32 * 32; e += blockDim.x) {
+        const int jj = e >> 5, cc = e & 31;
+        Ws[e] = (j0 + jj < k0 && c0 + cc < Nc) ? W[(j0 + jj) * N + c0 + cc] : T::zero();
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int jj = 0; jj < 32; ++jj) {
+        const A w = Ws[jj * 32 + lane];
+#pragma unroll
+        for (int q = 0; q < NB / 8; ++q) acc[q] = T::fms(acc[q], Cs[(warp + 8 * q) * 32 + jj], w);
+      }
+      __syncthreads();
+    }
   }
 #pragma unroll
   for (int q = 0; q < NB / 8; ++q) Ys[(warp + 8 * q) * 32 + lane] = acc[q];
   __syncthreads();
 
-  // n_i = (Y_i - sum_{i'<i} beta[i][i'] n_i') / s_i
-  if (warp == 0 && cval) {
-    for (int ii = 0; ii < nbr; ++ii) {
-      A y = Ys[ii * 32 + lane];
-      for (int ip = 0; ip < ii; ++ip) y = T::fms(y, bs[ii * NB + ip], Ys[ip * 32 + lane]);
-      Ys[ii * 32 + lane] = T::div(y, ps[ii]);
-    }
+  // Bot = S^-1 Y
+#pragma unroll
+  for (int q = 0; q < NB / 8; ++q) {
+    const int ii = warp + 8 * q;
+    A v = T::zero();
+    for (int ip = 0; ip < nbr; ++ip) v = T::fms(v, Si[ii * NB + ip], Ys[ip * 32 + lane]);
+    Bs[ii * 32 + lane] = T::neg(v);
   }
   __syncthreads();
 
-  if (cval) {
-    // old rows: W0_T - Wsave n
+  if constexpr (std::is_same<A, cdf>::value) {
+    // old rows, Karatsuba with lazy accumulators (as for Y): Top = W0_T - W0_P Bot
+    df* Bsum = (df*)(mj + 32) + NB * 32 + 32 * 32;
+    A* Wrow = (A*)(Bsum + NB * 32) + warp * 32;          // this warp's W0_P row
+    df* Wrs = (df*)((A*)(Bsum + NB * 32) + 8 * 32) + warp * 32;
+    for (int e = tid; e < NB * 32; e += blockDim.x) Bsum[e] = df_add(Bs[e].re, Bs[e].im);
+    __syncthreads();
+    for (int64_t j = warp; j < k0; j += 8) {
+      if (lane < nbr) {
+        const A wv = W0P[j * NB + lane];
+        Wrow[lane] = wv;
+        Wrs[lane] = df_add(wv.re, wv.im);
+      }
+      __syncwarp();
+      lzf S1{0.f, 0.f}, S2{0.f, 0.f}, S3{0.f, 0.f};
+      for (int ii = 0; ii < nbr; ++ii) {
+        const A bv = Bs[ii * 32 + lane];
+        const A wv = Wrow[ii];
+        lz_mac(S1, wv.re, bv.re);
+        lz_mac(S2, wv.im, bv.im);
+        lz_mac(S3, Wrs[ii], Bsum[ii * 32 + lane]);
+      }
+      if (cval) {
+        const df p1 = lz_get(S1), p2 = lz_get(S2), p3 = lz_get(S3);
+        const A v = W[j * N + c];
+        W[j * N + c] = A{df_sub(v.re, df_sub(p1, p2)), df_sub(v.im, df_sub(df_sub(p3, p1), p2))};
+      }
+      __syncwarp();
+    }
+    if (cval)
+      for (int jn = warp; jn < nbr; jn += 8) W[(k0 + jn) * N + c] = Bs[jn * 32 + lane];
+  } else if (cval) {
+    // old rows: Top = W0_T - W0_P Bot
     for (int64_t j = warp; j < k0; j += 8) {
       A v = W[j * N + c];
-      const A* ws = WsT + j * NB;
-      for (int ii = 0; ii < nbr; ++ii) v = T::fms(v, ws[ii], Ys[ii * 32 + lane]);
+      const A* wp = W0P + j * NB;
+      for (int ii = 0; ii < nbr; ++ii) v = T::fms(v, wp[ii], Bs[ii * 32 + lane]);
       W[j * N + c] = v;
     }
-    // new rows: n_j - sum_{i>j} w_{k0+i}[k0+j] n_i
-    for (int jn = warp; jn < nbr; jn += 8) {
-      A v = Ys[jn * 32 + lane];
-      const A* ws = WsT + (k0 + jn) * NB;
-      for (int ii = jn + 1; ii < nbr; ++ii) v = T::fms(v, ws[ii], Ys[ii * 32 + lane]);
-      W[(k0 + jn) * N + c] = v;
-    }
+    // new rows: Bot
+    for (int jn = warp; jn < nbr; jn += 8) W[(k0 + jn) * N + c] = Bs[jn * 32 + lane];
   }
   __syncthreads();
 
@@ -249,7 +559,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   if (op_mode != kOpNone && cb == 0 && k1 < a.n_steps) {
     for (int64_t j = tid; j <= k1; j += blockDim.x) {
       const A v = (j < k1) ? T::neg(W[j * N + k1]) : T::one();
-      put_h(a, op_mode, b, mrow[j], T::out(v));
+      put_state<A>(a, op_mode, b, mrow[j], v);
     }
   }
 }
@@ -261,21 +571,42 @@ __global__ void __launch_bounds__(256) tail_panel_kernel(StepArgs a, BlockedArgs
   panel_body<A>(a, t, blockIdx.y, blockIdx.x, k0, k1, op_mode, smem_raw);
 }
 
-static size_t step_smem(int64_t Nc, size_t es) { return (size_t)Nc * (2 * es + 4) + (8 * 32 + 32) * es; }
-static size_t panel_smem(size_t es) { return (size_t)(NB * 32 * 2 + 32 * 32 + NB * NB + NB) * es + (NB + 32) * 4; }
+static size_t panel_s_smem(size_t es) {
+  return (size_t)(NB * 2 * NB + NB * 32 + 32 * NB + NB + 1) * es + 2 * NB * 4;
+}
+// Ys, Bs, Cs, Ws, S^-1, the two index arrays, then (double-float) the Karatsuba sums of
+// C, W and Bot and the per-warp staged W0_P rows with their sums.
+static size_t panel_smem(size_t es) {
+  return (size_t)(NB * 32 * 3 + 32 * 32 + NB * NB) * es + 2 * 32 * 4 + (size_t)(NB * 32 * 2 + 32 * 32) * 8 +
+         (size_t)8 * 32 * (es + 8);
+}
 
-// Grouped forms: CTA blockIdx.x -> (instance, sample[, column block]) through the entry list.
+// ------------------------------------------------------------------ grouped forms
 template <typename A>
 __global__ void __launch_bounds__(256)
     step_group_kernel(const GroupInst* __restrict__ inst, const GroupEntry* __restrict__ ent, int n, int op_mode) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ DrawShared dsh;
   const int64_t item = blockIdx.x;
   const int e = group_find(ent, n, item);
   const GroupInst* gi = inst + ent[e].inst;
   const StepArgs a = gi->a;
   const BlockedArgs t = gi->t;
-  step_body<A>(a, t, item - ent[e].start, ent[e].k, op_mode, smem_raw, dsh);
+  const int64_t b = (item - ent[e].start) * kStepWarps + (threadIdx.x >> 5);
+  if (b >= a.bw) return;
+  step_warp<A>(a, t, b, ent[e].k, op_mode);
+}
+
+template <typename A>
+__global__ void __launch_bounds__(256)
+    panel_s_group_kernel(const GroupInst* __restrict__ inst, const GroupEntry* __restrict__ ent, int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t item = blockIdx.x;
+  const int e = group_find(ent, n, item);
+  const GroupInst* gi = inst + ent[e].inst;
+  const StepArgs a = gi->a;
+  const BlockedArgs t = gi->t;
+  const int64_t k = ent[e].k;
+  const int64_t k0 = (k / NB) * NB, k1 = min(k0 + NB, t.Nc);
+  panel_s_body<A>(a, t, item - ent[e].start, k0, k1, smem_raw);
 }
 
 template <typename A>
@@ -294,10 +625,38 @@ __global__ void __launch_bounds__(256)
   panel_body<A>(a, t, local / ncb, local % ncb, k0, k1, op_mode, smem_raw);
 }
 
+// ------------------------------------------------------------------ launchers
+#define FFS_DISPATCH_STATE(cplx, state, F, ...)                       \
+  ((cplx) ? ((state) == kStateFP64   ? F<cd>(__VA_ARGS__)            \
+             : (state) == kStateFP32 ? F<cf>(__VA_ARGS__)            \
+                                     : F<cdf>(__VA_ARGS__))          \
+          : ((state) == kStateFP64   ? F<double>(__VA_ARGS__)        \
+             : (state) == kStateFP32 ? F<float>(__VA_ARGS__)         \
+                                     : F<df>(__VA_ARGS__)))
+
+template <typename A>
+static cudaError_t step_t(const StepArgs& a, const BlockedArgs& t, int64_t k, int op, cudaStream_t s) {
+  tail_step_kernel<A><<<(unsigned)((a.bw + kStepWarps - 1) / kStepWarps), 32 * kStepWarps, 0, s>>>(a, t, k, op);
+  return cudaGetLastError();
+}
+template <typename A>
+static cudaError_t panel_t(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int op, cudaStream_t s) {
+  tail_panel_s_kernel<A><<<(unsigned)a.bw, 256, panel_s_smem(sizeof(A)), s>>>(a, t, k0, k1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((t.Nc - k1 + 31) / 32), (unsigned)a.bw);
+  tail_panel_kernel<A><<<grid, 256, panel_smem(sizeof(A)), s>>>(a, t, k0, k1, op);
+  return cudaGetLastError();
+}
 template <typename A>
 static cudaError_t group_step_t(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op,
-                                int64_t maxNc, cudaStream_t s) {
-  step_group_kernel<A><<<(unsigned)total, 256, step_smem(maxNc, sizeof(A)), s>>>(inst, e, n, op);
+                                cudaStream_t s) {
+  step_group_kernel<A><<<(unsigned)total, 32 * kStepWarps, 0, s>>>(inst, e, n, op);
+  return cudaGetLastError();
+}
+template <typename A>
+static cudaError_t group_panel_s_t(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, cudaStream_t s) {
+  panel_s_group_kernel<A><<<(unsigned)total, 256, panel_s_smem(sizeof(A)), s>>>(inst, e, n);
   return cudaGetLastError();
 }
 template <typename A>
@@ -307,30 +666,34 @@ static cudaError_t group_panel_t(const GroupInst* inst, const GroupEntry* e, int
   return cudaGetLastError();
 }
 
+cudaError_t launch_blocked_step(const StepArgs& a, const BlockedArgs& t, int64_t k, int state, int op,
+                                cudaStream_t s) {
+  return FFS_DISPATCH_STATE(a.cplx, state, step_t, a, t, k, op, s);
+}
+
+cudaError_t launch_blocked_panel(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int state,
+                                 int op, cudaStream_t s) {
+  if (k1 >= t.Nc) return cudaSuccess;
+  return FFS_DISPATCH_STATE(a.cplx, state, panel_t, a, t, k0, k1, op, s);
+}
+
 cudaError_t launch_group_step(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, bool cplx,
                               int state, int op, int64_t maxNc, cudaStream_t s) {
+  (void)maxNc;
   if (total <= 0) return cudaSuccess;
-  if (cplx) {
-    if (state == kStateFP64) return group_step_t<cd>(inst, e, n, total, op, maxNc, s);
-    if (state == kStateFP32) return group_step_t<cf>(inst, e, n, total, op, maxNc, s);
-    return group_step_t<cdf>(inst, e, n, total, op, maxNc, s);
-  }
-  if (state == kStateFP64) return group_step_t<double>(inst, e, n, total, op, maxNc, s);
-  if (state == kStateFP32) return group_step_t<float>(inst, e, n, total, op, maxNc, s);
-  return group_step_t<df>(inst, e, n, total, op, maxNc, s);
+  return FFS_DISPATCH_STATE(cplx, state, group_step_t, inst, e, n, total, op, s);
+}
+
+cudaError_t launch_group_panel_s(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, bool cplx,
+                                 int state, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  return FFS_DISPATCH_STATE(cplx, state, group_panel_s_t, inst, e, n, total, s);
 }
 
 cudaError_t launch_group_panel(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, bool cplx,
                                int state, int op, cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
-  if (cplx) {
-    if (state == kStateFP64) return group_panel_t<cd>(inst, e, n, total, op, s);
-    if (state == kStateFP32) return group_panel_t<cf>(inst, e, n, total, op, s);
-    return group_panel_t<cdf>(inst, e, n, total, op, s);
-  }
-  if (state == kStateFP64) return group_panel_t<double>(inst, e, n, total, op, s);
-  if (state == kStateFP32) return group_panel_t<float>(inst, e, n, total, op, s);
-  return group_panel_t<df>(inst, e, n, total, op, s);
+  return FFS_DISPATCH_STATE(cplx, state, group_panel_t, inst, e, n, total, op, s);
 }
 
 size_t blocked_elem_bytes(bool cplx, int state) {
@@ -338,48 +701,13 @@ size_t blocked_elem_bytes(bool cplx, int state) {
   return cplx ? 2 * base : base;
 }
 
-
-template <typename A>
-static cudaError_t launch_step_t(const StepArgs& a, const BlockedArgs& t, int64_t k, int op, cudaStream_t s) {
-  tail_step_kernel<A><<<(unsigned)a.bw, 256, step_smem(t.Nc, sizeof(A)), s>>>(a, t, k, op);
-  return cudaGetLastError();
-}
-template <typename A>
-static cudaError_t launch_panel_t(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int op,
-                                  cudaStream_t s) {
-  dim3 grid((unsigned)((t.Nc - k1 + 31) / 32), (unsigned)a.bw);
-  tail_panel_kernel<A><<<grid, 256, panel_smem(sizeof(A)), s>>>(a, t, k0, k1, op);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_blocked_step(const StepArgs& a, const BlockedArgs& t, int64_t k, int state, int op,
-                                cudaStream_t s) {
-  if (a.cplx) {
-    if (state == kStateFP64) return launch_step_t<cd>(a, t, k, op, s);
-    if (state == kStateFP32) return launch_step_t<cf>(a, t, k, op, s);
-    return launch_step_t<cdf>(a, t, k, op, s);
-  }
-  if (state == kStateFP64) return launch_step_t<double>(a, t, k, op, s);
-  if (state == kStateFP32) return launch_step_t<float>(a, t, k, op, s);
-  return launch_step_t<df>(a, t, k, op, s);
-}
-
-cudaError_t launch_blocked_panel(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int state,
-                                 int op, cudaStream_t s) {
-  if (k1 >= t.Nc) return cudaSuccess;
-  if (a.cplx) {
-    if (state == kStateFP64) return launch_panel_t<cd>(a, t, k0, k1, op, s);
-    if (state == kStateFP32) return launch_panel_t<cf>(a, t, k0, k1, op, s);
-    return launch_panel_t<cdf>(a, t, k0, k1, op, s);
-  }
-  if (state == kStateFP64) return launch_panel_t<double>(a, t, k0, k1, op, s);
-  if (state == kStateFP32) return launch_panel_t<float>(a, t, k0, k1, op, s);
-  return launch_panel_t<df>(a, t, k0, k1, op, s);
-}
-
 int blocked_panel_width() { return NB; }
+int blocked_step_samples_per_cta() { return kStepWarps; }
 
-size_t blocked_step_smem(int64_t Nc, bool cplx, int state) { return step_smem(Nc, blocked_elem_bytes(cplx, state)); }
+size_t blocked_step_smem(int64_t Nc, bool cplx, int state) {
+  (void)Nc;
+  return panel_smem(blocked_elem_bytes(cplx, state));
+}
 
 template <typename K> static cudaError_t allow_smem(K kernel, int optin) {
   cudaFuncAttributes at;
@@ -388,34 +716,24 @@ template <typename K> static cudaError_t allow_smem(K kernel, int optin) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)at.sharedSizeBytes);
 }
 
+template <typename A> static cudaError_t allow_all(int optin) {
+  cudaError_t e = allow_smem(tail_panel_s_kernel<A>, optin);
+  if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<A>, optin);
+  if (e == cudaSuccess) e = allow_smem(panel_s_group_kernel<A>, optin);
+  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<A>, optin);
+  return e;
+}
+
 cudaError_t configure_blocked() {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = allow_smem(tail_step_kernel<double>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_step_kernel<float>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_step_kernel<df>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_step_kernel<cd>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_step_kernel<cf>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_step_kernel<cdf>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<double>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<float>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<df>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<cd>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<cf>, optin);
-  if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<cdf>, optin);
-  if (e == cudaSuccess) e = allow_smem(step_group_kernel<double>, optin);
-  if (e == cudaSuccess) e = allow_smem(step_group_kernel<float>, optin);
-  if (e == cudaSuccess) e = allow_smem(step_group_kernel<df>, optin);
-  if (e == cudaSuccess) e = allow_smem(step_group_kernel<cd>, optin);
-  if (e == cudaSuccess) e = allow_smem(step_group_kernel<cf>, optin);
-  if (e == cudaSuccess) e = allow_smem(step_group_kernel<cdf>, optin);
-  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<double>, optin);
-  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<float>, optin);
-  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<df>, optin);
-  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<cd>, optin);
-  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<cf>, optin);
-  if (e == cudaSuccess) e = allow_smem(panel_group_kernel<cdf>, optin);
+  if (e == cudaSuccess) e = allow_all<double>(optin);
+  if (e == cudaSuccess) e = allow_all<float>(optin);
+  if (e == cudaSuccess) e = allow_all<df>(optin);
+  if (e == cudaSuccess) e = allow_all<cd>(optin);
+  if (e == cudaSuccess) e = allow_all<cf>(optin);
+  if (e == cudaSuccess) e = allow_all<cdf>(optin);
   return e;
 }
 
