@@ -149,6 +149,7 @@ static void release(ffs_ctx* c) {
   cudaFree(c->Ue_lo);
   cudaFree(c->Ue_tf32);
   cudaFree(c->UT32);
+  cudaFree(c->Ust);
   cudaFree(c->status);
   if (c->status_host) cudaFreeHost(c->status_host);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -321,6 +322,11 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
   if (op == kOpTF32) CREATE_TRY(cudaMalloc((void**)&c->Ue_tf32, emb * 4));
   if (op == kOpNone) CREATE_TRY(cudaMalloc(&c->UT32, (size_t)L * N * (cplx ? 8 : 4)));
   CREATE_TRY(launch_derive_operands(c, c->stream));
+  if (blocked(c) && state_kind(c) != kStateFP64) {
+    const size_t es = blocked_elem_bytes(cplx, state_kind(c));
+    CREATE_TRY(cudaMalloc(&c->Ust, (size_t)L * N * es));
+    CREATE_TRY(launch_derive_state_copy(c->U64, cplx, state_kind(c), L * N, c->Ust, c->stream));
+  }
   CREATE_TRY(cudaMalloc((void**)&c->status, sizeof(int)));
   CREATE_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
   CREATE_TRY(cudaMallocHost((void**)&c->status_host, sizeof(int)));
@@ -408,6 +414,7 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
     a.first = first_sample_index + (uint64_t)b0;
     a.cplx = h->cplx;
     a.U64 = h->U64;
+    a.Ust = h->Ust ? h->Ust : h->U64;
     a.m = h->m;
     a.mask = h->mask;
     a.H = h->H;
@@ -436,6 +443,11 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
     FFS_CUDA_TRY(h, cudaMemsetAsync(h->mask, 0, (size_t)bw * h->ldMask * 4, st));
     FFS_CUDA_TRY(h, cudaMemsetAsync(h->logp, 0, (size_t)bw * 8, st));
     TIMED(h, FFS_PHASE_PERM, st, launch_perm_init(a, op, st));
+    if (!plain && op != kOpF32 && b0 == 0) {
+      // column tile of the tensor-core residual: autotuned once per size class
+      const int bn = residual_tile_for(h, a, op, st);
+      FFS_CUDA_TRY(h, prepare_residual_tc_bn(h, op, bn));
+    }
     for (int64_t k = 0; k < n_steps; ++k) {
       if (plain)
         TIMED(h, FFS_PHASE_RESIDUAL, st, launch_residual_plain(a, h->UT32, k, st));

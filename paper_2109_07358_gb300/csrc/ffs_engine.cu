@@ -54,6 +54,7 @@ void fill_inst(GroupInst& g, ffs_ctx* c, int64_t B, uint64_t seed, uint64_t firs
   a.first = first;
   a.cplx = c->cplx;
   a.U64 = c->U64;
+  a.Ust = c->Ust ? c->Ust : c->U64;
   a.m = c->m;
   a.mask = c->mask;
   a.H = c->H;
@@ -80,8 +81,24 @@ void fill_inst(GroupInst& g, ffs_ctx* c, int64_t B, uint64_t seed, uint64_t firs
   p.P = c->P;
   p.mask = c->mask;
   p.status = c->status;
-  g.n_jtiles = c->Lrp / residual_tile_cols();
+  g.bn = c->res_bn ? c->res_bn : 256;
+  g.n_jtiles = c->Lrp / g.bn;
   g.n_btiles = (B + 127) / 128;
+}
+
+// Pick (autotune on first use) the residual column tile of handle c for B samples and
+// encode its tensor maps; then fill its group descriptor.
+cudaError_t tune_and_fill(GroupInst& g, ffs_ctx* c, int64_t B, uint64_t seed, int32_t* x, int64_t n_steps,
+                          cudaStream_t st) {
+  const int op = ctx_op_mode(c);
+  cudaError_t e = prepare_residual_tc(c, op);
+  if (e != cudaSuccess) return e;
+  fill_inst(g, c, B, seed, 0, x, n_steps);
+  const int bn = residual_tile_for(c, g.a, op, st);
+  e = prepare_residual_tc_bn(c, op, bn);
+  if (e != cudaSuccess) return e;
+  fill_inst(g, c, B, seed, 0, x, n_steps);
+  return cudaSuccess;
 }
 
 enum LaunchKind { kInit = 0, kResidual = 1, kStep = 2, kPanelS = 3, kPanelUpd = 4 };
@@ -91,6 +108,7 @@ struct Launch {
   int64_t off;    // first entry in the entry buffer
   int n;          // entries
   int64_t total;  // work items
+  int bn;         // residual column tile of the instances in this launch
 };
 
 // Builder of one launch's entry list.
@@ -99,8 +117,9 @@ struct LaunchBuilder {
   std::vector<Launch>& launches;
   int kind;
   int64_t off, total = 0;
-  LaunchBuilder(std::vector<GroupEntry>& e, std::vector<Launch>& l, int k)
-      : ents(e), launches(l), kind(k), off((int64_t)e.size()) {}
+  int bn = 0;
+  LaunchBuilder(std::vector<GroupEntry>& e, std::vector<Launch>& l, int k, int tile = 0)
+      : ents(e), launches(l), kind(k), off((int64_t)e.size()), bn(tile) {}
   void add(int inst, int64_t k, int64_t items) {
     if (items <= 0) return;
     ents.push_back(GroupEntry{total, inst, (int32_t)k});
@@ -108,7 +127,7 @@ struct LaunchBuilder {
   }
   void done() {
     const int n = (int)((int64_t)ents.size() - off);
-    if (n > 0) launches.push_back(Launch{kind, off, n, total});
+    if (n > 0) launches.push_back(Launch{kind, off, n, total, bn});
   }
 };
 
@@ -132,7 +151,7 @@ cudaError_t issue(const Launch& L, const GroupInst* d_inst, const GroupEntry* d_
   const GroupEntry* e = d_ent + L.off;
   switch (L.kind) {
     case kInit: return launch_group_init(d_inst, e, L.n, L.total, op, s);
-    case kResidual: return launch_group_residual(d_inst, e, L.n, L.total, op, s);
+    case kResidual: return launch_group_residual(d_inst, e, L.n, L.total, op, L.bn, s);
     case kStep: return launch_group_step(d_inst, e, L.n, L.total, cplx, state, op, maxNc, s);
     case kPanelS: return launch_group_panel_s(d_inst, e, L.n, L.total, cplx, state, s);
     case kPanelUpd: return launch_group_panel(d_inst, e, L.n, L.total, cplx, state, op, s);
@@ -183,10 +202,9 @@ extern "C" int ffs_sample_batched(ffs_handle* hs, const int64_t* Bs, const uint6
     ffs_ctx* c = hs[i];
     int r = ctx_ensure_workspace(c, Bs[i]);
     if (r != FFS_OK) return r;
-    cudaError_t e = prepare_residual_tc(c, op);
-    if (e != cudaSuccess) return ctx_fail(c0, FFS_E_CUDA, std::string("ffs_sample_batched: ") + cudaGetErrorString(e));
     GroupInst g;
-    fill_inst(g, c, Bs[i], seeds[i], 0, outs[i], c->N);
+    cudaError_t e = tune_and_fill(g, c, Bs[i], seeds[i], outs[i], c->N, st);
+    if (e != cudaSuccess) return ctx_fail(c0, FFS_E_CUDA, std::string("ffs_sample_batched: ") + cudaGetErrorString(e));
     inst.push_back(g);
     Ns.push_back(c->N);
     Bv.push_back(Bs[i]);
@@ -202,10 +220,12 @@ extern "C" int ffs_sample_batched(ffs_handle* hs, const int64_t* Bs, const uint6
     lb.done();
   }
   for (int64_t k = 0; k < maxN; ++k) {
-    LaunchBuilder res(ents, launches, kResidual);
-    for (int i = 0; i < ni; ++i)
-      if (k < Ns[i]) res.add(i, k, inst[i].n_btiles * inst[i].n_jtiles);
-    res.done();
+    for (int tile : {256, 128}) {
+      LaunchBuilder res(ents, launches, kResidual, tile);
+      for (int i = 0; i < ni; ++i)
+        if (k < Ns[i] && inst[i].bn == tile) res.add(i, k, inst[i].n_btiles * inst[i].n_jtiles);
+      res.done();
+    }
     LaunchBuilder stp(ents, launches, kStep);
     for (int i = 0; i < ni; ++i)
       if (k < Ns[i]) stp.add(i, k, step_items(Bv[i]));
@@ -328,8 +348,10 @@ size_t request_footprint(const Request& r, unsigned flags) {
   probe.Lrp = (probe.Lr + 255) / 256 * 256;
   probe.ldP = (r.L + 3) / 4 * 4;
   probe.ldMask = (r.L + 31) / 32;
-  const size_t fixed = (size_t)r.L * r.N * (probe.cplx ? 16 : 8) +
-                       (size_t)probe.Lrp * probe.Kp * ctx_op_elem_bytes(ctx_op_mode(&probe));
+  size_t fixed = (size_t)r.L * r.N * (probe.cplx ? 16 : 8) +
+                 (size_t)probe.Lrp * probe.Kp * ctx_op_elem_bytes(ctx_op_mode(&probe));
+  if (ctx_state_kind(&probe) != kStateFP64)  // copy of U in the state type
+    fixed += (size_t)r.L * r.N * blocked_elem_bytes(probe.cplx, ctx_state_kind(&probe));
   return fixed + (size_t)r.n * (ctx_per_sample_bytes(&probe) + (size_t)r.N * 4) + ((size_t)1 << 20);
 }
 
@@ -356,8 +378,11 @@ bool admit(ffs_server* s, Request* r) {
   }
   rc = ctx_ensure_workspace(r->h, r->n);
   cudaError_t e = cudaSuccess;
-  if (rc == FFS_OK) e = prepare_residual_tc(r->h, ctx_op_mode(r->h));
-  if (rc == FFS_OK && e == cudaSuccess) e = cudaMalloc((void**)&r->xdev, (size_t)r->n * r->N * 4);
+  if (rc == FFS_OK) e = cudaMalloc((void**)&r->xdev, (size_t)r->n * r->N * 4);
+  if (rc == FFS_OK && e == cudaSuccess) {
+    GroupInst g;
+    e = tune_and_fill(g, r->h, r->n, r->seed, r->xdev, r->N, s->stream);
+  }
   if (rc != FFS_OK || e != cudaSuccess) {
     finish(s, r, rc != FFS_OK ? rc : FFS_E_NOMEM, "ffs_submit: could not set up the request on the device");
     return false;
@@ -419,9 +444,12 @@ void engine_loop(ffs_server* s) {
         lb.done();
       }
       {
-        LaunchBuilder res(ents, launches, kResidual);
-        for (int i = 0; i < ni; ++i) res.add(i, members[i]->k, inst[i].n_btiles * inst[i].n_jtiles);
-        res.done();
+        for (int tile : {256, 128}) {
+          LaunchBuilder res(ents, launches, kResidual, tile);
+          for (int i = 0; i < ni; ++i)
+            if (inst[i].bn == tile) res.add(i, members[i]->k, inst[i].n_btiles * inst[i].n_jtiles);
+          res.done();
+        }
         LaunchBuilder stp(ents, launches, kStep);
         for (int i = 0; i < ni; ++i) stp.add(i, members[i]->k, step_items(members[i]->n));
         stp.done();

@@ -24,6 +24,7 @@ struct alignas(64) GroupInst {
   TcArgs tc;
   int64_t n_jtiles;    // residual tiles along the embedding columns
   int64_t n_btiles;    // residual tiles along the samples
+  int64_t bn;          // residual column tile of this instance (128 or 256)
 };
 
 __device__ __forceinline__ int group_find(const GroupEntry* __restrict__ e, int n, int64_t item) {
@@ -39,7 +40,7 @@ __device__ __forceinline__ int group_find(const GroupEntry* __restrict__ e, int 
 // ceil(bw/8) (a warp per sample); panel S bw; panel bw * ceil((Nc - k1)/32).
 cudaError_t launch_group_init(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op,
                               cudaStream_t s);
-cudaError_t launch_group_residual(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op,
+cudaError_t launch_group_residual(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op, int bn,
                                   cudaStream_t s);
 cudaError_t launch_group_step(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, bool cplx,
                               int state, int op, int64_t maxNc, cudaStream_t s);

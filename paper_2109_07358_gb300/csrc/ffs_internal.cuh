@@ -151,6 +151,7 @@ struct ffs_ctx {
   __nv_bfloat16* Ue_lo = nullptr;
   float* Ue_tf32 = nullptr;        // TF32-rounded FP32 plane (TF32 form)
   void* UT32 = nullptr;     // N x L float / cf: columns of U, contiguous in y (plain form)
+  void* Ust = nullptr;      // L x N in the blocked state's type when it is not FP64 (owned)
   int64_t Lr = 0, Kr = 0;   // real-embedding sizes: (L, N) real, (2L, 2N) complex
   int64_t Kp = 0;           // Kr padded to the tensor-core K tile
   int64_t Lrp = 0;          // Lr padded to the tensor-core site tile
@@ -178,7 +179,8 @@ struct ffs_ctx {
   // TMA descriptors of the tensor-core residual: the two planes of Ue and of H.
   CUtensorMap tmU[2];
   CUtensorMap tmH[2];
-  int tm_U_ready = -1;   // operand mode tmU was encoded for
+  int tm_U_ready = -1;   // operand mode * 1000 + column tile that tmU was encoded for
+  int res_bn = 0;        // residual column tile in use (0: not chosen yet)
   int64_t tm_H_B = -1;   // workspace capacity tmH was encoded for
   int* status = nullptr;         // device status word
   int* status_host = nullptr;    // pinned mirror

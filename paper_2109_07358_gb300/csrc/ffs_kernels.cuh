@@ -22,6 +22,7 @@ struct StepArgs {
   uint64_t seed, first;    // Philox key; global index of the wave's first sample
   bool cplx;
   const void* U64;         // L x N (double / cd)
+  const void* Ust;         // L x N in the blocked state's type (the FP64 copy for FP64 states)
   const int32_t* m;        // bw x N
   uint32_t* mask;          // bw x ldMask
   void* H;                 // bw x Kp operand planes
@@ -61,6 +62,8 @@ cudaError_t launch_perm_init(const StepArgs& a, int op_mode, cudaStream_t s);
 cudaError_t launch_ortho_check(const void* U64, bool cplx, int64_t L, int64_t N, double* maxdev,
                                cudaStream_t s);
 cudaError_t launch_derive_operands(ffs_ctx* c, cudaStream_t s);
+// Copy of U in the blocked state's arithmetic type (double-float or FP32); FP64 states use U64.
+cudaError_t launch_derive_state_copy(const void* U64, bool cplx, int state, int64_t count, void* out, cudaStream_t s);
 cudaError_t launch_residual_fp32(const StepArgs& a, const float* Ue32, cudaStream_t s);
 cudaError_t launch_residual_plain(const StepArgs& a, const void* UT32, int64_t k, cudaStream_t s);
 // state_fp64: FP64 (double / cd) state, else FP32 (float / cf).

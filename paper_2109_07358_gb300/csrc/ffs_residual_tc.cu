@@ -20,6 +20,12 @@
 // lanes of its rank mod 4).
 #include <cudaTypedefs.h>
 
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+
 #include "ffs_group.cuh"
 #include "ffs_residual_tc.cuh"
 #include "ffs_sm100.cuh"
@@ -270,21 +276,32 @@ static cudaError_t encode_2d(CUtensorMap* map, const void* base, bool f32, uint6
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-constexpr int kBN = 256;
+// Tile configurations (embedding columns per CTA, pipeline stages) for each precision;
+// the autotuner picks the column tile per size class.
+template <int KIND, int BN> struct StagesOf;
+template <> struct StagesOf<kKindBF16x3, 256> { static constexpr int v = 2; };
+template <> struct StagesOf<kKindBF16x3, 128> { static constexpr int v = 3; };
+template <> struct StagesOf<kKindBF16, 256> { static constexpr int v = 4; };
+template <> struct StagesOf<kKindBF16, 128> { static constexpr int v = 6; };
+template <> struct StagesOf<kKindTF32, 256> { static constexpr int v = 4; };
+template <> struct StagesOf<kKindTF32, 128> { static constexpr int v = 6; };
 
-cudaError_t prepare_residual_tc(ffs_ctx* c, int op) {
+static int kind_of(int op) { return op == kOpBF16x3 ? kKindBF16x3 : op == kOpBF16 ? kKindBF16 : kKindTF32; }
+
+cudaError_t prepare_residual_tc_bn(ffs_ctx* c, int op, int bn) {
   const bool f32 = (op == kOpTF32);
-  if (c->tm_U_ready != op) {
+  const int key = op * 1000 + bn;
+  if (c->tm_U_ready != key) {
     const void* u0 = f32 ? (const void*)c->Ue_tf32 : (const void*)c->Ue_hi;
-    cudaError_t e = encode_2d(&c->tmU[0], u0, f32, c->Kp, c->Lrp, kBN);
+    cudaError_t e = encode_2d(&c->tmU[0], u0, f32, c->Kp, c->Lrp, bn);
     if (e != cudaSuccess) return e;
     if (op == kOpBF16x3) {
-      e = encode_2d(&c->tmU[1], c->Ue_lo, false, c->Kp, c->Lrp, kBN);
+      e = encode_2d(&c->tmU[1], c->Ue_lo, false, c->Kp, c->Lrp, bn);
       if (e != cudaSuccess) return e;
     } else {
       c->tmU[1] = c->tmU[0];
     }
-    c->tm_U_ready = op;
+    c->tm_U_ready = key;
   }
   if (c->tm_H_B != c->ws_B) {
     const uint64_t plane = (uint64_t)c->ws_B * c->Kp;
@@ -298,11 +315,17 @@ cudaError_t prepare_residual_tc(ffs_ctx* c, int op) {
     }
     c->tm_H_B = c->ws_B;
   }
+  c->res_bn = bn;
   return cudaSuccess;
 }
 
-template <int BN, int STAGES, int KIND>
+cudaError_t prepare_residual_tc(ffs_ctx* c, int op) {
+  return prepare_residual_tc_bn(c, op, c->res_bn ? c->res_bn : 256);
+}
+
+template <int BN, int KIND>
 static cudaError_t launch_cfg(ffs_ctx* c, const StepArgs& a, cudaStream_t s) {
+  constexpr int STAGES = StagesOf<KIND, BN>::v;
   using Cf = TcCfg<BN, STAGES, KIND>;
   TcArgs p;
   p.bw = a.bw;
@@ -319,61 +342,152 @@ static cudaError_t launch_cfg(ffs_ctx* c, const StepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual_tc(ffs_ctx* c, const StepArgs& a, int op, cudaStream_t s) {
-  cudaError_t e = prepare_residual_tc(c, op);
-  if (e != cudaSuccess) return e;
-  switch (op) {
-    case kOpBF16x3: return launch_cfg<kBN, 2, kKindBF16x3>(c, a, s);
-    case kOpBF16: return launch_cfg<kBN, 4, kKindBF16>(c, a, s);
-    case kOpTF32: return launch_cfg<kBN, 4, kKindTF32>(c, a, s);
-    default: return cudaErrorInvalidValue;
+static cudaError_t launch_bn(ffs_ctx* c, const StepArgs& a, int op, int bn, cudaStream_t s) {
+  switch (kind_of(op) * 2 + (bn == 128 ? 1 : 0)) {
+    case kKindBF16x3 * 2: return launch_cfg<256, kKindBF16x3>(c, a, s);
+    case kKindBF16x3 * 2 + 1: return launch_cfg<128, kKindBF16x3>(c, a, s);
+    case kKindBF16 * 2: return launch_cfg<256, kKindBF16>(c, a, s);
+    case kKindBF16 * 2 + 1: return launch_cfg<128, kKindBF16>(c, a, s);
+    case kKindTF32 * 2: return launch_cfg<256, kKindTF32>(c, a, s);
+    default: return launch_cfg<128, kKindTF32>(c, a, s);
   }
 }
 
-cudaError_t launch_group_residual(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op,
+// ------------------------------------------------------------------ autotuner
+// Size class -> column tile, measured once per process (CUDA events on the launching
+// stream, two candidates, best of three launches each) and optionally kept in the file
+// named by FFS_TUNE_CACHE ("key tile" lines).  FFS_RES_BN=128|256 forces a tile.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+static bool g_tune_loaded = false;
+
+// Size classes: power-of-two buckets of the embedding rows, K and sample tiles, so that a
+// stream of requests of varied sizes reuses a handful of measurements.
+static int64_t pow2_ceil(int64_t v) {
+  int64_t b = 1;
+  while (b < v) b <<= 1;
+  return b;
+}
+static std::string tune_key(int op, int64_t Lrp, int64_t Kp, int64_t bw) {
+  return std::to_string(op) + ":" + std::to_string(pow2_ceil(Lrp)) + ":" + std::to_string(pow2_ceil(Kp)) + ":" +
+         std::to_string(pow2_ceil((bw + 127) / 128));
+}
+
+static void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("FFS_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char key[128];
+  int bn;
+  while (fscanf(f, "%127s %d", key, &bn) == 2)
+    if (bn == 128 || bn == 256) g_tune[key] = bn;
+  fclose(f);
+}
+
+static void tune_store(const std::string& key, int bn) {
+  const char* path = getenv("FFS_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d\n", key.c_str(), bn);
+  fclose(f);
+}
+
+int residual_tile_for(ffs_ctx* c, const StepArgs& a, int op, cudaStream_t s) {
+  const char* forced = getenv("FFS_RES_BN");
+  if (forced && (atoi(forced) == 128 || atoi(forced) == 256)) return atoi(forced);
+  const std::string key = tune_key(op, c->Lrp, c->Kp, a.bw);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  int best = 256;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return best;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return best;
+  }
+  for (int bn : {256, 128}) {
+    if (prepare_residual_tc_bn(c, op, bn) != cudaSuccess || launch_bn(c, a, op, bn, s) != cudaSuccess) continue;
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, s);
+      launch_bn(c, a, op, bn, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms_min = ms < ms_min ? ms : ms_min;
+    }
+    if (ms_min < best_ms) {
+      best_ms = ms_min;
+      best = bn;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (!g_tune.count(key)) {
+    g_tune[key] = best;
+    tune_store(key, best);
+  }
+  return best;
+}
+
+cudaError_t launch_residual_tc(ffs_ctx* c, const StepArgs& a, int op, cudaStream_t s) {
+  const int bn = c->res_bn ? c->res_bn : 256;
+  cudaError_t e = prepare_residual_tc_bn(c, op, bn);
+  if (e != cudaSuccess) return e;
+  return launch_bn(c, a, op, bn, s);
+}
+
+template <int BN, int KIND>
+static void group_launch(const GroupInst* inst, const GroupEntry* e, int n, unsigned grid, cudaStream_t s) {
+  constexpr int STAGES = StagesOf<KIND, BN>::v;
+  residual_group_kernel<BN, STAGES, KIND><<<grid, 192, TcCfg<BN, STAGES, KIND>::SMEM, s>>>(inst, e, n);
+}
+
+cudaError_t launch_group_residual(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, int op, int bn,
                                   cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)total;
-  switch (op) {
-    case kOpBF16x3:
-      residual_group_kernel<kBN, 2, kKindBF16x3><<<grid, 192, TcCfg<kBN, 2, kKindBF16x3>::SMEM, s>>>(inst, e, n);
-      break;
-    case kOpBF16:
-      residual_group_kernel<kBN, 4, kKindBF16><<<grid, 192, TcCfg<kBN, 4, kKindBF16>::SMEM, s>>>(inst, e, n);
-      break;
-    case kOpTF32:
-      residual_group_kernel<kBN, 4, kKindTF32><<<grid, 192, TcCfg<kBN, 4, kKindTF32>::SMEM, s>>>(inst, e, n);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+  switch (kind_of(op) * 2 + (bn == 128 ? 1 : 0)) {
+    case kKindBF16x3 * 2: group_launch<256, kKindBF16x3>(inst, e, n, grid, s); break;
+    case kKindBF16x3 * 2 + 1: group_launch<128, kKindBF16x3>(inst, e, n, grid, s); break;
+    case kKindBF16 * 2: group_launch<256, kKindBF16>(inst, e, n, grid, s); break;
+    case kKindBF16 * 2 + 1: group_launch<128, kKindBF16>(inst, e, n, grid, s); break;
+    case kKindTF32 * 2: group_launch<256, kKindTF32>(inst, e, n, grid, s); break;
+    default: group_launch<128, kKindTF32>(inst, e, n, grid, s); break;
   }
   return cudaGetLastError();
 }
 
-int residual_tile_cols() { return kBN; }
 int residual_k_block(int op) { return op == kOpTF32 ? 32 : 64; }
 
+template <int BN, int KIND> static cudaError_t allow_cfg() {
+  constexpr int STAGES = StagesOf<KIND, BN>::v;
+  constexpr int SM = TcCfg<BN, STAGES, KIND>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(residual_tc_kernel<BN, STAGES, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(residual_group_kernel<BN, STAGES, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+  return e;
+}
+
 cudaError_t configure_residual_tc() {
-  {
-    cudaError_t e = cudaFuncSetAttribute(residual_group_kernel<kBN, 2, kKindBF16x3>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<kBN, 2, kKindBF16x3>::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(residual_group_kernel<kBN, 4, kKindBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               TcCfg<kBN, 4, kKindBF16>::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(residual_group_kernel<kBN, 4, kKindTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               TcCfg<kBN, 4, kKindTF32>::SMEM);
-    if (e != cudaSuccess) return e;
-  }
-  cudaError_t e;
-  e = cudaFuncSetAttribute(residual_tc_kernel<kBN, 2, kKindBF16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           TcCfg<kBN, 2, kKindBF16x3>::SMEM);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(residual_tc_kernel<kBN, 4, kKindBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           TcCfg<kBN, 4, kKindBF16>::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(residual_tc_kernel<kBN, 4, kKindTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              TcCfg<kBN, 4, kKindTF32>::SMEM);
+  cudaError_t e = allow_cfg<256, kKindBF16x3>();
+  if (e == cudaSuccess) e = allow_cfg<128, kKindBF16x3>();
+  if (e == cudaSuccess) e = allow_cfg<256, kKindBF16>();
+  if (e == cudaSuccess) e = allow_cfg<128, kKindBF16>();
+  if (e == cudaSuccess) e = allow_cfg<256, kKindTF32>();
+  if (e == cudaSuccess) e = allow_cfg<128, kKindTF32>();
+  return e;
 }
 
 }  // namespace fermi

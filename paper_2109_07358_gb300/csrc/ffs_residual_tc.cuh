@@ -18,9 +18,11 @@ struct TcArgs {
 // P[b, y] = |sum_c H[b, c] Ue[j, c]|^2 on tcgen05 tensor cores (operand encoding op).
 cudaError_t launch_residual_tc(ffs_ctx* c, const StepArgs& a, int op, cudaStream_t s);
 cudaError_t configure_residual_tc();
-// Encode the tensor maps of c for operand mode op (no-op when already current).
-cudaError_t prepare_residual_tc(ffs_ctx* c, int op);
-int residual_tile_cols();        // embedding columns per CTA tile
+// Encode the tensor maps of c for operand mode op and column tile bn (no-op when current).
+cudaError_t prepare_residual_tc(ffs_ctx* c, int op);  // keeps the tile chosen before (256 if none)
+cudaError_t prepare_residual_tc_bn(ffs_ctx* c, int op, int bn);
+// Column tile (128 or 256) for this size class: autotuned on first use, then cached.
+int residual_tile_for(ffs_ctx* c, const StepArgs& a, int op, cudaStream_t s);
 int residual_k_block(int op);    // K elements per 128-byte TMA row
 
 }  // namespace fermi

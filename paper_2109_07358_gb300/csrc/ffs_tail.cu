@@ -171,7 +171,6 @@ template <typename A>
 __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k,
                                           int op_mode) {
   using T = Ar<A>;
-  using U = typename T::U;
   const int lane = threadIdx.x & 31;
   const int64_t L = a.L, N = a.N, Nc = t.Nc;
   const float* __restrict__ prow = a.P + b * a.ldP;
@@ -218,7 +217,7 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
   A* W = (A*)t.W + (size_t)b * N * N;
   A* W0P = (A*)t.W0P + (size_t)b * N * NB;
   const int32_t* mrow = a.m + b * N;
-  const U* urow = (const U*)a.U64 + (int64_t)x * N;
+  const A* urow = (const A*)a.Ust + (int64_t)x * N;  // U in the state type
   const int64_t c = k + lane;
   const bool cval = c < k1;
 
@@ -231,7 +230,7 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
   A acc = T::zero(), acc2 = T::zero();
   for (int64_t j0 = 0; j0 < k; j0 += 32) {
     const int64_t jl = j0 + lane;
-    const A uj = (jl < k) ? T::from(urow[mrow[jl]]) : T::zero();
+    const A uj = (jl < k) ? urow[mrow[jl]] : T::zero();
     const int jn = (int)min((int64_t)32, k - j0);
     int jj = 0;
     for (; jj + 8 <= jn; jj += 8) {
@@ -250,7 +249,7 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
     }
   }
   acc = T::add(acc, acc2);
-  const A rc = cval ? T::add(T::from(urow[mrow[c]]), acc) : T::zero();
+  const A rc = cval ? T::add(urow[mrow[c]], acc) : T::zero();
   const A s = shfl_idx_any(rc, 0);  // pivot: the Schur residual of x_k
   if (lane == 0) {
     const double s2 = T::abs2(s);
@@ -308,7 +307,6 @@ template <typename A>
 __device__ __forceinline__ void panel_s_body(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k0,
                                              int64_t k1, unsigned char* smem_raw) {
   using T = Ar<A>;
-  using U = typename T::U;
   A* Aug = (A*)smem_raw;        // NB x 2NB: [S | I] -> [I | S^-1]
   A* Cs = Aug + NB * 2 * NB;    // NB x 32 chunk of U[x_new, m_j]
   A* Ws = Cs + NB * 32;         // 32 x NB chunk of W0_P
@@ -319,7 +317,7 @@ __device__ __forceinline__ void panel_s_body(const StepArgs& a, const BlockedArg
   const int64_t N = a.N;
   const int nbr = (int)(k1 - k0);
   const int32_t* mrow = a.m + b * N;
-  const U* U64 = (const U*)a.U64;
+  const A* Us = (const A*)a.Ust;  // U in the state type
   const A* W0P = (const A*)t.W0P + (size_t)b * N * NB;
   if (tid < NB) xs[tid] = tid < nbr ? a.x[b * a.n_steps + k0 + tid] : 0;
   __syncthreads();
@@ -329,14 +327,14 @@ __device__ __forceinline__ void panel_s_body(const StepArgs& a, const BlockedArg
 #pragma unroll
   for (int q = 0; q < NB / 8; ++q) {
     const int ii = r0 + 8 * q;
-    acc[q] = (ii < nbr && cc < nbr) ? T::from(U64[(int64_t)xs[ii] * N + mrow[k0 + cc]]) : T::zero();
+    acc[q] = (ii < nbr && cc < nbr) ? Us[(int64_t)xs[ii] * N + mrow[k0 + cc]] : T::zero();
   }
   for (int64_t j0 = 0; j0 < k0; j0 += 32) {
     if (tid < 32) mj[tid] = (j0 + tid < k0) ? mrow[j0 + tid] : 0;
     __syncthreads();
     for (int e = tid; e < NB * 32; e += blockDim.x) {
       const int ii = e >> 5, jj = e & 31;
-      Cs[e] = (ii < nbr && j0 + jj < k0) ? T::from(U64[(int64_t)xs[ii] * N + mj[jj]]) : T::zero();
+      Cs[e] = (ii < nbr && j0 + jj < k0) ? Us[(int64_t)xs[ii] * N + mj[jj]] : T::zero();
       Ws[e] = (j0 + ii < k0 && jj < nbr) ? W0P[(j0 + ii) * NB + jj] : T::zero();  // row ii of the chunk
     }
     __syncthreads();
@@ -388,7 +386,6 @@ template <typename A>
 __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t cb,
                                            int64_t k0, int64_t k1, int op_mode, unsigned char* smem_raw) {
   using T = Ar<A>;
-  using U = typename T::U;
   A* Ys = (A*)smem_raw;     // NB x 32: Y
   A* Bs = Ys + NB * 32;     // NB x 32: Bot
   A* Cs = Bs + NB * 32;     // NB x 32: U[x_new, m_j] chunk
@@ -405,7 +402,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   A* W = (A*)t.W + (size_t)b * N * N;
   const A* W0P = (const A*)t.W0P + (size_t)b * N * NB;
   const int32_t* mrow = a.m + b * N;
-  const U* U64 = (const U*)a.U64;
+  const A* Us = (const A*)a.Ust;  // U in the state type
 
   for (int e = tid; e < NB * NB; e += blockDim.x) Si[e] = ((const A*)t.Sinv)[(size_t)b * NB * NB + e];
   if (tid < NB) xs[tid] = tid < nbr ? a.x[b * a.n_steps + k0 + tid] : 0;
@@ -417,7 +414,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
 #pragma unroll
   for (int q = 0; q < NB / 8; ++q) {
     const int ii = warp + 8 * q;
-    acc[q] = (ii < nbr && cval) ? T::from(U64[(int64_t)xs[ii] * N + mc]) : T::zero();
+    acc[q] = (ii < nbr && cval) ? Us[(int64_t)xs[ii] * N + mc] : T::zero();
   }
   if constexpr (std::is_same<A, cdf>::value || std::is_same<A, df>::value) {
     // double-float: lazily renormalised accumulators; complex products by Karatsuba
@@ -434,7 +431,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
       __syncthreads();
       for (int e = tid; e < NB * 32; e += blockDim.x) {
         const int ii = e >> 5, jj = e & 31;
-        const A v = (ii < nbr && j0 + jj < k0) ? T::from(U64[(int64_t)xs[ii] * N + mj[jj]]) : T::zero();
+        const A v = (ii < nbr && j0 + jj < k0) ? Us[(int64_t)xs[ii] * N + mj[jj]] : T::zero();
         Cs[e] = v;
         if constexpr (CX) Csum[e] = df_add(v.re, v.im);
       }
@@ -481,7 +478,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
       __syncthreads();
       for (int e = tid; e < NB * 32; e += blockDim.x) {
         const int ii = e >> 5, jj = e & 31;
-        Cs[e] = (ii < nbr && j0 + jj < k0) ? T::from(U64[(int64_t)xs[ii] * N + mj[jj]]) : T::zero();
+        Cs[e] = (ii < nbr && j0 + jj < k0) ? Us[(int64_t)xs[ii] * N + mj[jj]] : T::zero();
       }
       for (int e = tid; e < 32 * 32; e += blockDim.x) {
         const int jj = e >> 5, cc = e & 31;
@@ -694,6 +691,29 @@ cudaError_t launch_group_panel(const GroupInst* inst, const GroupEntry* e, int n
                                int state, int op, cudaStream_t s) {
   if (total <= 0) return cudaSuccess;
   return FFS_DISPATCH_STATE(cplx, state, group_panel_t, inst, e, n, total, op, s);
+}
+
+__global__ void state_copy_kernel(const void* U64, bool cplx, int state, int64_t count, void* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    if (cplx) {
+      const cd u = ((const cd*)U64)[e];
+      if (state == kStateDF64)
+        ((cdf*)out)[e] = cdf{df_from(u.re), df_from(u.im)};
+      else
+        ((cf*)out)[e] = cf{(float)u.re, (float)u.im};
+    } else {
+      const double u = ((const double*)U64)[e];
+      if (state == kStateDF64)
+        ((df*)out)[e] = df_from(u);
+      else
+        ((float*)out)[e] = (float)u;
+    }
+  }
+}
+
+cudaError_t launch_derive_state_copy(const void* U64, bool cplx, int state, int64_t count, void* out, cudaStream_t s) {
+  state_copy_kernel<<<1024, 256, 0, s>>>(U64, cplx, state, count, out);
+  return cudaGetLastError();
 }
 
 size_t blocked_elem_bytes(bool cplx, int state) {

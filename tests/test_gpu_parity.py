@@ -228,3 +228,17 @@ def test_errors_are_reported():
         S.sync()
     assert e.value.code == ffs.FFS_E_ARG
     S.sync()  # the status word was cleared
+
+
+def test_residual_tile_widths_agree(monkeypatch):
+    """The autotuner's two column tiles (128 and 256) give bit-identical samples: each
+    weight's K reduction runs in the same order whatever the tile width."""
+    U = w.haar(700, 90, seed=12)
+    outs = {}
+    for bn in ("128", "256"):
+        monkeypatch.setenv("FFS_RES_BN", bn)
+        S = sampler(U, ffs.FFS_RES_BF16X3 | ffs.FFS_STATE_DF64)
+        outs[bn] = S.sample(150, 4)["x"].cpu().numpy()
+        S.sync()
+        S.close()
+    assert np.array_equal(outs["128"], outs["256"])
