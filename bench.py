@@ -311,6 +311,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-samples", type=int, default=0)
     ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-marginal", action="store_true")
+    ap.add_argument("--marginal-steps", type=int, default=128)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
@@ -487,6 +489,20 @@ def main():
                                "sample": f"{n} samples of the same workload (indices 0..{n - 1}), "
                                          f"{wall:.1f} s wall"}
 
+    if not args.no_marginal and rank == 0:
+        # marginal sampling: the first n of the N positions (the chain stopped after n steps)
+        nm = min(args.marginal_steps, N)
+        xm = torch.empty((B, nm), dtype=torch.int32, device="cuda")
+        ffs.ffs_sample_ex(S.h, B, 0, 0, nm, xm, stream=stream)
+        S.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ffs.ffs_sample_ex(S.h, B, 0, 0, nm, xm, stream=stream)
+        e1.record(stream)
+        S.sync()
+        mms = e0.elapsed_time(e1)
+        out["marginal"] = {"n_steps": nm, "samples_per_s": B / (mms / 1e3), "ms_per_batch": mms,
+                           "full_chain_ms_per_batch": ms_step}
     S.close()
     if not args.no_batching and rank == 0:
         out["batching"] = bench_batching(args, flags, stream)

@@ -83,21 +83,26 @@ static bool blocked(const ffs_ctx* c) {
 static size_t state_elem_bytes(const ffs_ctx* c) { return blocked_elem_bytes(c->cplx, state_kind(c)); }
 
 // Device bytes per sample of a wave (not counting optional outputs).
-static size_t per_sample_bytes(const ffs_ctx* c) {
+// Device bytes per sample of a wave (not counting optional outputs) for a chain of Nc
+// steps: the blocked state keeps Nc x Nc entries, the unblocked one N x N.
+static size_t state_cols(const ffs_ctx* c, int64_t Nc) { return blocked(c) ? (size_t)Nc : (size_t)c->N; }
+static size_t per_sample_bytes_nc(const ffs_ctx* c, int64_t Nc) {
   const int op = op_mode_of(c->flags);
+  const size_t sc = state_cols(c, Nc);
   size_t b = 0;
   b += (size_t)c->N * 4;                           // m
   b += (size_t)c->ldMask * 4;                      // mask
   b += (size_t)c->Kp * op_elem_bytes(op);          // operand planes
   b += (size_t)c->ldP * 4;                         // weights
-  b += (size_t)c->N * c->N * state_elem_bytes(c);  // elimination state
+  b += sc * sc * state_elem_bytes(c);              // elimination state
   b += 8;                                          // logp
   if (blocked(c)) {                                // panel-start columns, panel inverse
     const size_t nb = blocked_panel_width();
-    b += ((size_t)c->N * nb + nb * nb) * state_elem_bytes(c);
+    b += (sc * nb + nb * nb) * state_elem_bytes(c);
   }
   return b;
 }
+static size_t per_sample_bytes(const ffs_ctx* c) { return per_sample_bytes_nc(c, c->N); }
 
 static void free_workspace(ffs_ctx* c) {
   cudaFree(c->m);
@@ -117,27 +122,39 @@ static void free_workspace(ffs_ctx* c) {
   c->W = nullptr;
   c->logp = nullptr;
   c->ws_B = 0;
+  c->W_bytes = 0;
+  c->W0P_bytes = 0;
 }
 
-static int ensure_workspace(ffs_ctx* c, int64_t Bw) {
-  if (Bw <= c->ws_B) return FFS_OK;
+// Buffers for Bw samples of a chain of Nc steps; the state buffers are sized in bytes so
+// that short (marginal) chains fit more samples.
+static int ensure_workspace_nc(ffs_ctx* c, int64_t Bw, int64_t Nc) {
+  const size_t sc = state_cols(c, Nc), es = state_elem_bytes(c), nb = blocked_panel_width();
+  const size_t w_need = (size_t)Bw * sc * sc * es;
+  const size_t w0_need = blocked(c) ? (size_t)Bw * sc * nb * es : 0;
+  if (Bw <= c->ws_B && w_need <= c->W_bytes && w0_need <= c->W0P_bytes) return FFS_OK;
   cudaStreamSynchronize(c->stream);
+  const int64_t B = Bw > c->ws_B ? Bw : c->ws_B;
+  const size_t wb = w_need > c->W_bytes ? w_need : c->W_bytes;
+  const size_t w0b = w0_need > c->W0P_bytes ? w0_need : c->W0P_bytes;
   free_workspace(c);
   const int op = op_mode_of(c->flags);
-  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->m, (size_t)Bw * c->N * 4));
-  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->mask, (size_t)Bw * c->ldMask * 4));
-  if (op != kOpNone) FFS_CUDA_TRY(c, cudaMalloc(&c->H, (size_t)Bw * c->Kp * op_elem_bytes(op)));
-  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->P, (size_t)Bw * c->ldP * 4));
-  FFS_CUDA_TRY(c, cudaMalloc(&c->W, (size_t)Bw * c->N * c->N * state_elem_bytes(c)));
-  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->logp, (size_t)Bw * 8));
+  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->m, (size_t)B * c->N * 4));
+  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->mask, (size_t)B * c->ldMask * 4));
+  if (op != kOpNone) FFS_CUDA_TRY(c, cudaMalloc(&c->H, (size_t)B * c->Kp * op_elem_bytes(op)));
+  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->P, (size_t)B * c->ldP * 4));
+  FFS_CUDA_TRY(c, cudaMalloc(&c->W, wb));
+  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->logp, (size_t)B * 8));
   if (blocked(c)) {
-    const size_t nb = blocked_panel_width(), es = state_elem_bytes(c);
-    FFS_CUDA_TRY(c, cudaMalloc(&c->W0P, (size_t)Bw * c->N * nb * es));
-    FFS_CUDA_TRY(c, cudaMalloc(&c->Sinv, (size_t)Bw * nb * nb * es));
+    FFS_CUDA_TRY(c, cudaMalloc(&c->W0P, w0b));
+    FFS_CUDA_TRY(c, cudaMalloc(&c->Sinv, (size_t)B * nb * nb * es));
   }
-  c->ws_B = Bw;
+  c->ws_B = B;
+  c->W_bytes = wb;
+  c->W0P_bytes = w0b;
   return FFS_OK;
 }
+static int ensure_workspace(ffs_ctx* c, int64_t Bw) { return ensure_workspace_nc(c, Bw, c->N); }
 
 static void release(ffs_ctx* c) {
   if (!c) return;
@@ -373,7 +390,7 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
                         (out_probs && !probs_dev);
 
   // Wave size from free device memory.
-  size_t per = per_sample_bytes(h);
+  size_t per = per_sample_bytes_nc(h, n_steps);
   if (!x_dev) per += n_steps * 4;
   if (force_x && !force_dev) per += n_steps * 4;
   if (out_probs && !probs_dev) per += (size_t)n_steps * h->L * 4;
@@ -381,12 +398,12 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
   FFS_CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t reserve = (size_t)512 << 20;
   size_t have = free_b > reserve ? free_b - reserve : 0;
-  have += (size_t)h->ws_B * per_sample_bytes(h);  // the workspace we already hold is reusable
+  have += (size_t)h->ws_B * per_sample_bytes_nc(h, n_steps);  // the workspace we already hold is reusable
   int64_t Bw = (int64_t)(have / per);
   if (Bw < 1) return fail(h, FFS_E_NOMEM, "ffs_sample_ex: not enough device memory for one sample");
   if (Bw > B) Bw = B;
-  if (Bw > h->ws_B) {
-    int r = ensure_workspace(h, Bw);
+  {
+    int r = ensure_workspace_nc(h, Bw, n_steps);
     if (r != FFS_OK) return r;
   }
   int32_t* xbuf = nullptr;

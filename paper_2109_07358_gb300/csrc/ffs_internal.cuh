@@ -158,6 +158,7 @@ struct ffs_ctx {
 
   // Workspace for one wave of samples (grown on demand).
   int64_t ws_B = 0;
+  size_t W_bytes = 0, W0P_bytes = 0;  // capacities of the state buffers
   int64_t ws_steps = 0;
   int32_t* m = nullptr;          // Bw x N column orders
   uint32_t* mask = nullptr;      // Bw x ceil(L/32) chosen-site bits

@@ -214,8 +214,9 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
   if (k + 1 >= a.n_steps) return;
 
   const int64_t k0 = (k / NB) * NB, i = k - k0, k1 = min(k0 + NB, Nc);
-  A* W = (A*)t.W + (size_t)b * N * N;
-  A* W0P = (A*)t.W0P + (size_t)b * N * NB;
+  const int64_t ldw = Nc;  // the state keeps Nc x Nc entries per sample
+  A* W = (A*)t.W + (size_t)b * Nc * Nc;
+  A* W0P = (A*)t.W0P + (size_t)b * Nc * NB;
   const int32_t* mrow = a.m + b * N;
   const A* urow = (const A*)a.Ust + (int64_t)x * N;  // U in the state type
   const int64_t c = k + lane;
@@ -223,7 +224,7 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
 
   // first step of a panel: keep the old rows' panel columns for the panel-end update
   if (i == 0 && k0 > 0 && lane < k1 - k0)
-    for (int64_t j = 0; j < k0; ++j) W0P[j * NB + lane] = W[j * N + k0 + lane];
+    for (int64_t j = 0; j < k0; ++j) W0P[j * NB + lane] = W[j * ldw + k0 + lane];
 
   // reduce the new row on the panel columns: r'[c] = u[c] - sum_{j<k} u[j] W[j][c]
   // (rows in groups of 8 whose loads are issued together; two accumulation chains)
@@ -236,7 +237,7 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
     for (; jj + 8 <= jn; jj += 8) {
       A wv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) wv[q] = cval ? W[(j0 + jj + q) * N + c] : T::zero();
+      for (int q = 0; q < 8; ++q) wv[q] = cval ? W[(j0 + jj + q) * ldw + c] : T::zero();
 #pragma unroll
       for (int q = 0; q < 8; q += 2) {
         acc = T::fms(acc, shfl_idx_any(uj, jj + q), wv[q]);
@@ -245,7 +246,7 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
     }
     for (; jj < jn; ++jj) {
       const A u = shfl_idx_any(uj, jj);
-      if (cval) acc = T::fms(acc, u, W[(j0 + jj) * N + c]);
+      if (cval) acc = T::fms(acc, u, W[(j0 + jj) * ldw + c]);
     }
   }
   acc = T::add(acc, acc2);
@@ -261,34 +262,34 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
   // rank-1 update of the panel columns (k, k1) with the old column k; then the new row
   for (int64_t j0 = 0; j0 < k; j0 += 32) {
     const int64_t jl = j0 + lane;
-    const A wj = (jl < k) ? W[jl * N + k] : T::zero();
+    const A wj = (jl < k) ? W[jl * ldw + k] : T::zero();
     const int jn = (int)min((int64_t)32, k - j0);
     int jj = 0;
     for (; jj + 8 <= jn; jj += 8) {
       A wv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) wv[q] = upd ? W[(j0 + jj + q) * N + c] : T::zero();
+      for (int q = 0; q < 8; ++q) wv[q] = upd ? W[(j0 + jj + q) * ldw + c] : T::zero();
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const A w = shfl_idx_any(wj, jj + q);
-        if (upd) W[(j0 + jj + q) * N + c] = T::fms(wv[q], w, ncv);
+        if (upd) W[(j0 + jj + q) * ldw + c] = T::fms(wv[q], w, ncv);
       }
     }
     for (; jj < jn; ++jj) {
       const A w = shfl_idx_any(wj, jj);
       if (upd) {
-        A* p = W + (j0 + jj) * N + c;
+        A* p = W + (j0 + jj) * ldw + c;
         *p = T::fms(*p, w, ncv);
       }
     }
   }
-  if (upd) W[k * N + c] = ncv;
+  if (upd) W[k * ldw + c] = ncv;
   __syncwarp();
 
   // operand of step k+1 while column k+1 is still inside this panel
   if (op_mode != kOpNone && k + 1 < k1) {
     for (int64_t j = lane; j <= k + 1; j += 32) {
-      const A v = (j <= k) ? T::neg(W[j * N + k + 1]) : T::one();
+      const A v = (j <= k) ? T::neg(W[j * ldw + k + 1]) : T::one();
       put_state<A>(a, op_mode, b, mrow[j], v);
     }
   }
@@ -318,7 +319,7 @@ __device__ __forceinline__ void panel_s_body(const StepArgs& a, const BlockedArg
   const int nbr = (int)(k1 - k0);
   const int32_t* mrow = a.m + b * N;
   const A* Us = (const A*)a.Ust;  // U in the state type
-  const A* W0P = (const A*)t.W0P + (size_t)b * N * NB;
+  const A* W0P = (const A*)t.W0P + (size_t)b * t.Nc * NB;
   if (tid < NB) xs[tid] = tid < nbr ? a.x[b * a.n_steps + k0 + tid] : 0;
   __syncthreads();
   // thread owns entries (ii, cc) = (tid / 32 + 8 q, tid % 32)
@@ -399,8 +400,9 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   const int64_t c0 = k1 + cb * 32;
   const int64_t c = c0 + lane;
   const bool cval = c < Nc;
-  A* W = (A*)t.W + (size_t)b * N * N;
-  const A* W0P = (const A*)t.W0P + (size_t)b * N * NB;
+  const int64_t ldw = Nc;
+  A* W = (A*)t.W + (size_t)b * Nc * Nc;
+  const A* W0P = (const A*)t.W0P + (size_t)b * Nc * NB;
   const int32_t* mrow = a.m + b * N;
   const A* Us = (const A*)a.Ust;  // U in the state type
 
@@ -437,7 +439,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
       }
       for (int e = tid; e < 32 * 32; e += blockDim.x) {
         const int jj = e >> 5, cc = e & 31;
-        const A v = (j0 + jj < k0 && c0 + cc < Nc) ? W[(j0 + jj) * N + c0 + cc] : T::zero();
+        const A v = (j0 + jj < k0 && c0 + cc < Nc) ? W[(j0 + jj) * ldw + c0 + cc] : T::zero();
         Ws[e] = v;
         if constexpr (CX) Wsum[e] = df_add(v.re, v.im);
       }
@@ -482,7 +484,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
       }
       for (int e = tid; e < 32 * 32; e += blockDim.x) {
         const int jj = e >> 5, cc = e & 31;
-        Ws[e] = (j0 + jj < k0 && c0 + cc < Nc) ? W[(j0 + jj) * N + c0 + cc] : T::zero();
+        Ws[e] = (j0 + jj < k0 && c0 + cc < Nc) ? W[(j0 + jj) * ldw + c0 + cc] : T::zero();
       }
       __syncthreads();
 #pragma unroll 4
@@ -532,30 +534,30 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
       }
       if (cval) {
         const df p1 = lz_get(S1), p2 = lz_get(S2), p3 = lz_get(S3);
-        const A v = W[j * N + c];
-        W[j * N + c] = A{df_sub(v.re, df_sub(p1, p2)), df_sub(v.im, df_sub(df_sub(p3, p1), p2))};
+        const A v = W[j * ldw + c];
+        W[j * ldw + c] = A{df_sub(v.re, df_sub(p1, p2)), df_sub(v.im, df_sub(df_sub(p3, p1), p2))};
       }
       __syncwarp();
     }
     if (cval)
-      for (int jn = warp; jn < nbr; jn += 8) W[(k0 + jn) * N + c] = Bs[jn * 32 + lane];
+      for (int jn = warp; jn < nbr; jn += 8) W[(k0 + jn) * ldw + c] = Bs[jn * 32 + lane];
   } else if (cval) {
     // old rows: Top = W0_T - W0_P Bot
     for (int64_t j = warp; j < k0; j += 8) {
-      A v = W[j * N + c];
+      A v = W[j * ldw + c];
       const A* wp = W0P + j * NB;
       for (int ii = 0; ii < nbr; ++ii) v = T::fms(v, wp[ii], Bs[ii * 32 + lane]);
-      W[j * N + c] = v;
+      W[j * ldw + c] = v;
     }
     // new rows: Bot
-    for (int jn = warp; jn < nbr; jn += 8) W[(k0 + jn) * N + c] = Bs[jn * 32 + lane];
+    for (int jn = warp; jn < nbr; jn += 8) W[(k0 + jn) * ldw + c] = Bs[jn * 32 + lane];
   }
   __syncthreads();
 
   // operand of step k1 (its column is the first of T)
   if (op_mode != kOpNone && cb == 0 && k1 < a.n_steps) {
     for (int64_t j = tid; j <= k1; j += blockDim.x) {
-      const A v = (j < k1) ? T::neg(W[j * N + k1]) : T::one();
+      const A v = (j < k1) ? T::neg(W[j * ldw + k1]) : T::one();
       put_state<A>(a, op_mode, b, mrow[j], v);
     }
   }
