@@ -29,15 +29,15 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     "lattice64x64_N1024_B4096": dict(
-        make="lattice", B=4096, L=4096, N=1024, cplx=True,
+        make="lattice", B=4096, L=4096, N=1024, cplx=True, grid=(64, 64),
         desc="64x64 open square lattice, random U(1) hopping phases (seed 0), N=1024 lowest orbitals, "
              "complex, B=4096 samples, Philox seed 0"),
     "lattice32x32_N256_B1024": dict(
-        make="lattice32", B=1024, L=1024, N=256, cplx=True,
+        make="lattice32", B=1024, L=1024, N=256, cplx=True, grid=(32, 32),
         desc="32x32 open square lattice, random U(1) hopping phases (seed 0), N=256 lowest orbitals, "
              "complex, B=1024 samples, Philox seed 0 (reduced case for profiler captures)"),
     "chain64_N8_B10000": dict(
-        make="chain", B=10000, L=64, N=8, cplx=False,
+        make="chain", B=10000, L=64, N=8, cplx=False, grid=(1, 64),
         desc="1D open chain L=64, N=8 (closed-form orbitals), B=10^4 samples, Philox seed 0"),
 }
 
@@ -259,6 +259,32 @@ def bench_batching(args, flags, stream):
             "launch": "one CUDA graph of grouped launches"}
 
 
+def bench_reweight(x, spec, stream, reps=20):
+    """Slater-Jastrow reweighting of the last timed batch: nearest-neighbour density-density
+    Jastrow (V = 0.05 per bond) and a random one-body observable, whole call timed
+    (kernels, result copy and synchronisation)."""
+    import torch
+
+    from paper_2109_07358_gb300 import ffs
+    from paper_2109_07358_gb300 import workloads as w
+
+    B, n_occ = int(x.shape[0]), int(x.shape[1])
+    nx, ny = spec["grid"]
+    v = tuple(torch.from_numpy(a).cuda() for a in w.neighbour_jastrow_csr(nx, ny, 0.05))
+    o = torch.from_numpy(np.random.default_rng(0).standard_normal(nx * ny)).cuda()
+    torch.cuda.synchronize()
+    ffs.ffs_jastrow_estimate(x, nx * ny, v, o, None, stream=stream)
+    walls = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        r = ffs.ffs_jastrow_estimate(x, nx * ny, v, o, None, stream=stream)
+        walls.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.median(walls))
+    return {"jastrow": f"nearest-neighbour, V=0.05 per bond, {int(v[2].numel())} entries", "B": B,
+            "n_occ": n_occ, "ms_per_call": ms, "samples_per_s": B / (ms / 1e3), "mean": r["mean"],
+            "ess": r["ess"], "timing": "host wall clock of the synchronous call, median of 20"}
+
+
 def bench_serving(args, flags):
     """Poisson stream of projection-DPP requests (U = top-N left singular vectors of L
     unit-norm Gaussian features of dimension D; L log-uniform [500, 20000], D in [64, 512],
@@ -314,6 +340,7 @@ def main():
     ap.add_argument("--no-marginal", action="store_true")
     ap.add_argument("--marginal-steps", type=int, default=128)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-reweight", action="store_true")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=300.0, help="serving arrivals per second")
@@ -503,6 +530,8 @@ def main():
         mms = e0.elapsed_time(e1)
         out["marginal"] = {"n_steps": nm, "samples_per_s": B / (mms / 1e3), "ms_per_batch": mms,
                            "full_chain_ms_per_batch": ms_step}
+    if not args.no_reweight and rank == 0:
+        out["reweight"] = bench_reweight(x, spec, stream)
     S.close()
     if not args.no_batching and rank == 0:
         out["batching"] = bench_batching(args, flags, stream)

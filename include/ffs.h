@@ -240,6 +240,49 @@ int ffs_wait(ffs_server* s, uint64_t req_id, int timeout_ms, double* latency_ms)
 int ffs_server_stats(ffs_server* s, int64_t* pending, int64_t* active, int64_t* iterations, size_t* bytes_in_use);
 void ffs_server_destroy(ffs_server* s);
 
+/*
+ * Slater-Jastrow reweighting (Supplementary Section S-5; Eq. 4 of the main text).
+ *
+ * A Jastrow state |psi_J> = J |phi_0>, J(x) = exp(-1/2 sum_ij v_ij n_i n_j), is not a
+ * determinant, but J is diagonal in the configuration basis, so expectations in it follow
+ * from samples x_b of the free-fermion state |phi_0> (drawn by ffs_sample) by reweighting:
+ *   <O>_J = <J^2 o_L>_0 / <J^2>_0,   J^2(x) = exp(-n^T v n).
+ * Observables are those diagonal in the configuration basis, whose local value is
+ *   o_L(x) = sum_i o_i n_i + sum_ij q_ij n_i n_j
+ * (densities, double occupancy, density-density correlations).
+ *
+ * Orbitals are the rows of U: for spinful fermions, sample each spin species with its
+ * own handle and offset the down-spin indices by the number of sites, so that the
+ * Gutzwiller factor of Eq. 4 is v_{i, L+i} = v_{L+i, i} = V/2.
+ *
+ *   x          device, B x n_occ int32, each row n_occ distinct orbitals in [0, n_orb)
+ *              in any order (an ffs_sample output, or several side by side).
+ *   v, q       sparse n_orb x n_orb matrices (struct below, all arrays device memory) or
+ *              NULL; the cost per sample is the summed row lengths of its orbitals, so
+ *              the Gutzwiller factor costs one entry per orbital and a dense matrix n_orb.
+ *   o          device, n_orb doubles, or NULL.
+ *   out_logj2  device, B doubles, or NULL: log J^2(x_b) per sample.
+ *   out_obs    device, B doubles, or NULL: o_L(x_b) per sample.
+ *   result     host or device, 4 doubles: <O>_J; log <J^2>_0; the effective sample size
+ *              (sum w)^2 / sum w^2 of the weights w_b = J^2(x_b); and the first-order
+ *              standard error sqrt(sum_b w_b^2 (o_L(x_b) - <O>_J)^2) / sum_b w_b.
+ * Reductions run in a fixed order, so equal inputs give equal results.  The call
+ * allocates stream-ordered scratch (2B + 4 doubles), runs on cuda_stream and
+ * synchronises it before returning.  FFS_E_ARG if a row of x names an orbital twice or
+ * outside [0, n_orb), or a CSR row pointer or column is out of range (the message is in
+ * ffs_last_error(NULL)); n_orb is limited to 1638400 (one bitmap per sample in shared
+ * memory).
+ */
+typedef struct {
+  const int64_t* rowptr; /* n_orb + 1 entries, non-decreasing, rowptr[n_orb] <= nnz */
+  const int32_t* col;    /* nnz column indices in [0, n_orb)                       */
+  const double* val;     /* nnz values                                             */
+  int64_t nnz;
+} ffs_csr;
+int ffs_jastrow_estimate(const int32_t* x, int64_t B, int64_t n_occ, int64_t n_orb, const ffs_csr* v,
+                         const double* o, const ffs_csr* q, double* out_logj2, double* out_obs, double* result,
+                         void* cuda_stream);
+
 /* Phases reported by ffs_profile_read. */
 #define FFS_PHASE_PERM 0      /* column orders m and the step-0 operand              */
 #define FFS_PHASE_RESIDUAL 1  /* all-site weights |u_y^T h|^2 (Section S-1 products) */

@@ -291,3 +291,66 @@ def pair_density(U) -> np.ndarray:
     R = np.outer(rho, rho) - np.abs(G) ** 2
     np.fill_diagonal(R, 0.0)
     return R
+
+
+# --------------------------------------------------------------------------------------
+# Slater-Jastrow reweighting (Supplementary Section S-5).
+#
+# |psi_J> = J |phi_0> with J = exp(-1/2 sum_ij v_ij n_i n_j) diagonal in the configuration
+# basis, so <psi_J|O|psi_J> / <psi_J|psi_J> becomes a ratio of free-fermion averages,
+# <J^2 o_L>_0 / <J^2>_0, where o_L(x) = <x|O|psi_J> / <x|psi_J>.  For an observable
+# diagonal in the configuration basis o_L(x) is its value on x; the ones handled here are
+# o_L(x) = sum_i o_i n_i + sum_ij q_ij n_i n_j.
+def occupations(X, n_orb: int) -> np.ndarray:
+    """B x n_orb matrix of the occupation numbers n_i (0 or 1) of each configuration."""
+    X = np.asarray(X, dtype=np.int64)
+    n = np.zeros((X.shape[0], n_orb))
+    n[np.arange(X.shape[0])[:, None], X] = 1.0
+    if np.any(n.sum(axis=1) != X.shape[1]):
+        raise ValueError("a configuration names an orbital twice")
+    return n
+
+
+def jastrow_log_weight(X, v) -> np.ndarray:
+    """log J^2(x) = -sum_ij v_ij n_i n_j for each configuration (v dense, n_orb x n_orb)."""
+    v = np.asarray(v, dtype=np.float64)
+    n = occupations(X, v.shape[0])
+    return -np.sum((n @ v) * n, axis=1)
+
+
+def diagonal_observable(X, n_orb: int, o=None, q=None) -> np.ndarray:
+    """o_L(x) = sum_i o_i n_i + sum_ij q_ij n_i n_j for each configuration."""
+    n = occupations(X, n_orb)
+    val = np.zeros(n.shape[0])
+    if o is not None:
+        val = val + n @ np.asarray(o, dtype=np.float64)
+    if q is not None:
+        val = val + np.sum((n @ np.asarray(q, dtype=np.float64)) * n, axis=1)
+    return val
+
+
+def jastrow_reweight(X, v, o=None, q=None) -> dict:
+    """The reweighting estimate of <O> in the Jastrow state from free-fermion samples X.
+
+    With weights w_b = J^2(x_b) (scaled by exp(-max log J^2), which cancels):
+      mean         sum_b w_b o_L(x_b) / sum_b w_b               = <J^2 o_L>_0 / <J^2>_0
+      log_j2_mean  log( (1/B) sum_b J^2(x_b) )                  = log <J^2>_0
+      ess          (sum_b w_b)^2 / sum_b w_b^2                  (effective sample size)
+      stderr       sqrt( sum_b w_b^2 (o_L(x_b) - mean)^2 ) / sum_b w_b
+                   (first-order error of a ratio of sample means)
+    plus the per-sample log J^2 and o_L."""
+    v = np.asarray(v, dtype=np.float64)
+    logj2 = jastrow_log_weight(X, v)
+    obs = diagonal_observable(X, v.shape[0], o, q)
+    mx = logj2.max()
+    w = np.exp(logj2 - mx)
+    sw = w.sum()
+    mean = float((w * obs).sum() / sw)
+    return {
+        "mean": mean,
+        "log_j2_mean": float(mx + math.log(sw / len(w))),
+        "ess": float(sw * sw / (w * w).sum()),
+        "stderr": float(math.sqrt(((w * (obs - mean)) ** 2).sum()) / sw),
+        "logj2": logj2,
+        "obs": obs,
+    }

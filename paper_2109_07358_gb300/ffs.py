@@ -45,6 +45,12 @@ class FFSError(RuntimeError):
         self.code = code
 
 
+class ffs_csr(ctypes.Structure):
+    """Sparse n x n matrix in CSR form; every array is device memory."""
+    _fields_ = [("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("nnz", ctypes.c_int64)]
+
+
 def lib() -> ctypes.CDLL:
     """Load libffs.so (built in-tree).  Raises when it is missing: there is no fallback."""
     global _lib
@@ -76,9 +82,11 @@ def lib() -> ctypes.CDLL:
         L.ffs_server_destroy.restype = None
         L.ffs_profile.argtypes = [vp, i32]
         L.ffs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]
+        L.ffs_jastrow_estimate.argtypes = [vp, i64, i64, i64, ctypes.POINTER(ffs_csr), vp, ctypes.POINTER(ffs_csr),
+                                           vp, vp, vp, vp]
         for name in ("ffs_create", "ffs_create_ex", "ffs_sample", "ffs_sample_ex", "ffs_sync", "ffs_query",
                      "ffs_profile", "ffs_profile_read", "ffs_sample_noalloc", "ffs_sample_batched",
-                     "ffs_server_create", "ffs_submit", "ffs_wait", "ffs_server_stats"):
+                     "ffs_server_create", "ffs_submit", "ffs_wait", "ffs_server_stats", "ffs_jastrow_estimate"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -213,6 +221,25 @@ def ffs_profile_read(h):
     n = (ctypes.c_int64 * FFS_NUM_PHASES)()
     _check(lib().ffs_profile_read(h, ms, n, FFS_NUM_PHASES), h)
     return {PHASE_NAMES[p]: (ms[p], n[p]) for p in range(FFS_NUM_PHASES)}
+
+
+def _csr(m):
+    if m is None:
+        return None
+    rowptr, col, val = m
+    return ctypes.byref(ffs_csr(rowptr.data_ptr(), col.data_ptr(), val.data_ptr(), int(val.numel())))
+
+
+def ffs_jastrow_estimate(x, n_orb: int, v=None, o=None, q=None, out_logj2=None, out_obs=None, stream=None):
+    """Reweighting estimate of a diagonal observable in the Jastrow state J |phi_0> from the
+    free-fermion samples x (device int32 tensor, B x n_occ).  v and q are (rowptr int64,
+    col int32, val float64) device tensors or None, o a float64 device tensor or None.
+    Returns {"mean", "log_j2_mean", "ess", "stderr"}."""
+    B, n_occ = int(x.shape[0]), int(x.shape[1])
+    res = (ctypes.c_double * 4)()
+    _check(lib().ffs_jastrow_estimate(_ptr(x), B, n_occ, int(n_orb), _csr(v), _ptr(o), _csr(q), _ptr(out_logj2),
+                                      _ptr(out_obs), ctypes.cast(res, ctypes.c_void_p), _stream(stream)))
+    return {"mean": res[0], "log_j2_mean": res[1], "ess": res[2], "stderr": res[3]}
 
 
 def dtype_of(U) -> int:

@@ -17,6 +17,10 @@ Workloads (sizes are parameters; the defaults are the ones the tests and the ben
                       feature rows (stand-in for the sentence embeddings of the
                       text-summarisation example; the real data is not available).
 * ``double_well``     the double-well chain of the supplementary double-well section.
+* ``anderson_square`` 2D open Anderson model (Eq. 5), one spin species; with
+                      ``gutzwiller_csr`` (Eq. 4) it gives the Anderson-Hubbard
+                      Slater-Jastrow workload (``anderson_hubbard_4x4``).
+* ``neighbour_jastrow_csr``  nearest-neighbour density-density Jastrow parameters.
 
 Matrices are float64 / complex128 and C-contiguous (row-major L x N).
 """
@@ -101,6 +105,68 @@ def anderson_chain(L: int, N: int, W: float = 1.0, seed: int = 0) -> np.ndarray:
         H = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
         return _lowest(H, N)
     return np.ascontiguousarray(v)
+
+
+def anderson_square_hamiltonian(nx: int, ny: int, W: float = 1.0, seed: int = 0) -> np.ndarray:
+    """One spin species of the 2D Anderson model of Eq. 5 on an open nx x ny square
+    lattice: hopping -1 on nearest-neighbour bonds, on-site w_i ~ U[-W, W] (site index
+    a = ix * ny + iy, energies drawn in site order)."""
+    L = nx * ny
+    H = np.diag(_rng(seed).uniform(-W, W, size=L))
+    for ix in range(nx):
+        for iy in range(ny):
+            a = ix * ny + iy
+            if ix + 1 < nx:
+                H[a, a + ny] = H[a + ny, a] = -1.0
+            if iy + 1 < ny:
+                H[a, a + 1] = H[a + 1, a] = -1.0
+    return H
+
+
+def anderson_square(nx: int, ny: int, N: int, W: float = 1.0, seed: int = 0) -> np.ndarray:
+    """Lowest-N orbitals (real, L = nx*ny) of ``anderson_square_hamiltonian``."""
+    return _lowest(anderson_square_hamiltonian(nx, ny, W, seed), N)
+
+
+def gutzwiller_csr(L: int, V: float):
+    """The Gutzwiller factor of Eq. 4 as Jastrow parameters over 2L spin-orbitals
+    (up-spin orbital i, down-spin orbital L + i): v_{i, L+i} = v_{L+i, i} = V/2, so that
+    1/2 sum_ij v_ij n_i n_j = (V/2) sum_i n_{i up} n_{i down}.  Returns CSR arrays
+    (row pointers int64, columns int32, values float64), one entry per row."""
+    rowptr = np.arange(2 * L + 1, dtype=np.int64)
+    col = np.concatenate([np.arange(L, 2 * L), np.arange(L)]).astype(np.int32)
+    val = np.full(2 * L, V / 2.0)
+    return rowptr, col, val
+
+
+def neighbour_jastrow_csr(nx: int, ny: int, V: float):
+    """A density-density Jastrow on an open nx x ny lattice (one orbital per site):
+    v_ab = V/2 on every nearest-neighbour bond (both directions).  CSR arrays as
+    ``gutzwiller_csr``."""
+    rows = []
+    for ix in range(nx):
+        for iy in range(ny):
+            nb = []
+            if ix > 0:
+                nb.append((ix - 1) * ny + iy)
+            if iy > 0:
+                nb.append(ix * ny + iy - 1)
+            if iy + 1 < ny:
+                nb.append(ix * ny + iy + 1)
+            if ix + 1 < nx:
+                nb.append((ix + 1) * ny + iy)
+            rows.append(nb)
+    rowptr = np.zeros(nx * ny + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.array([c for r in rows for c in r], dtype=np.int32)
+    return rowptr, col, np.full(col.size, V / 2.0)
+
+
+def anderson_hubbard_4x4(W: float = 1.0, seed: int = 0):
+    """The Anderson-Hubbard workload of the main text's correlated example: 4 x 4 open
+    lattice, N = 8 fermions taken as 4 per spin species, both species in the lowest four
+    orbitals of the same disordered Hamiltonian (Eq. 5)."""
+    return anderson_square(4, 4, 4, W, seed)
 
 
 def haar(L: int, N: int, seed: int = 0, complex_: bool = True) -> np.ndarray:
