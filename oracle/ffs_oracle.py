@@ -354,3 +354,64 @@ def jastrow_reweight(X, v, o=None, q=None) -> dict:
         "logj2": logj2,
         "obs": obs,
     }
+
+
+# --------------------------------------------------------------------------------------
+# L-ensemble DPP (main text, text-summarisation example): the correlation matrix
+# C = sum_j lambda_j u_j u_j^T; each eigenvector u_j is kept with probability
+# lambda_j / (lambda_j + 1), and the kept ones form the U of Eq. 1, sampled by FFS with
+# N = the number kept.
+# Reading: the keep decision of eigenvector j of sample s uses its own uniform, Philox
+# stream 2, block j, built like the site uniforms (53 bits); u < lambda / (lambda + 1)
+# keeps it (never for lambda <= 0).  The kept columns, in ascending order, are the U of
+# that sample, whose column order m is then drawn as for any other U (stream 0, with N =
+# the number kept).
+STREAM_SELECT = 2
+
+
+def select_uniform(seed: int, sample: int, j: int) -> float:
+    """The uniform in [0, 1) that decides whether eigenvector j is kept (Philox stream 2)."""
+    w = philox4x32_10(_ctr(j, STREAM_SELECT, sample), _key(seed))
+    return float(((w[0] >> 5) << 26) + (w[1] >> 6)) * 2.0**-53
+
+
+def lensemble_selection(lam, seed: int, sample: int) -> np.ndarray:
+    """Indices (ascending) of the eigenvectors kept by sample `sample`."""
+    keep = []
+    for j, lj in enumerate(np.asarray(lam, dtype=np.float64)):
+        p = lj / (lj + 1.0) if lj > 0 else 0.0
+        if select_uniform(seed, sample, j) < p:
+            keep.append(j)
+    return np.array(keep, dtype=np.int64)
+
+
+def lensemble_sample_one(V, lam, seed: int = 0, sample: int = 0, force_x=None, record: bool = False):
+    """One L-ensemble draw: the eigenvectors V[:, j] are kept as decided by
+    ``lensemble_selection``, then ``sample_one`` runs on U = V[:, kept] (its own column
+    order m over the kept columns).  Adds 'kept' (eigenvector indices) and 'm_full' (the
+    column order in V's columns: kept[m]) to the returned dict; an empty selection gives
+    an empty x."""
+    V = np.asarray(V)
+    kept = lensemble_selection(lam, seed, sample)
+    if kept.size == 0:
+        out = {"x": np.zeros(0, dtype=np.int64), "m": np.zeros(0, dtype=np.int64), "logp": 0.0}
+        if record:
+            out["probs"] = np.zeros((0, V.shape[0]))
+    else:
+        out = sample_one(V[:, kept], seed, sample, force_x=force_x, record=record)
+    out["kept"] = kept
+    out["m_full"] = kept[out["m"]]
+    return out
+
+
+def lensemble_set_probabilities(C) -> dict:
+    """Brute force over every subset S of the L items: P(S) = det(C_S) / det(C + I), the
+    L-ensemble with kernel C (sums to 1; the empty set has det = 1)."""
+    C = np.asarray(C, dtype=np.float64)
+    L = C.shape[0]
+    Z = np.linalg.det(C + np.eye(L))
+    out = {}
+    for n in range(L + 1):
+        for S in itertools.combinations(range(L), n):
+            out[S] = (np.linalg.det(C[np.ix_(S, S)]) if n else 1.0) / Z
+    return out

@@ -213,6 +213,16 @@ def lensemble_spectrum(Phi: np.ndarray):
     return s**2, np.ascontiguousarray(Uf)
 
 
+def lensemble_quality_features(L: int, D: int, alpha: float, seed: int = 0) -> np.ndarray:
+    """Quality-scaled feature rows b~_i = q_i b_i of the text-summarisation L-ensemble:
+    b_i unit-norm Gaussian rows of dimension D (stand-ins for sentence embeddings) and
+    qualities q_i = alpha exp(z_i / 2), z_i ~ N(0, 1) (stand-ins for the log-linear quality
+    model).  The kernel is C = Phi Phi^T; ``lensemble_spectrum`` gives its eigenpairs."""
+    Phi = lensemble_features(L, D, seed)
+    z = _rng(seed + 1).standard_normal(L)
+    return Phi * (alpha * np.exp(z / 2.0))[:, None]
+
+
 def double_well(L: int = 64, N: int = 4, c: float = 89.929, a: float = 4096.0, b: float = 2.0,
                 t: float = math.pi**2 / 6) -> np.ndarray:
     """Lowest-N orbitals of H = -t sum (c_i^+ c_{i+1} + h.c.) + sum_i V(x_i) n_i with
