@@ -285,6 +285,47 @@ def bench_reweight(x, spec, stream, reps=20):
             "ess": r["ess"], "timing": "host wall clock of the synchronous call, median of 20"}
 
 
+def bench_lensemble(flags, stream, B=4096, reps=3):
+    """L-ensemble DPP sampling (text-summarisation stand-in): L = 16384 items, D = 512
+    quality-scaled Gaussian features (alpha = 0.08, expected 126 kept eigenvectors), the
+    rank-512 eigenbasis on the device, B samples per call; each call keeps eigenvectors,
+    reads the longest chain back and runs the chains.  Host wall clock per call (the call
+    synchronises once inside) and CUDA-event time, median of `reps` after one warm-up."""
+    import torch
+
+    from paper_2109_07358_gb300 import ffs
+    from paper_2109_07358_gb300 import workloads as w
+
+    L, D, alpha = 16384, 512, 0.08
+    Phi = torch.from_numpy(w.lensemble_quality_features(L, D, alpha, seed=0)).cuda()
+    Uf, sv, _ = torch.linalg.svd(Phi, full_matrices=False)
+    lam = (sv * sv).contiguous()
+    V = Uf.contiguous()
+    torch.cuda.synchronize()
+    S = ffs.Sampler(V, flags, stream=stream)
+    S.sample_lensemble(lam, B, 0, stream=stream)
+    S.sync()
+    walls, evs = [], []
+    for r in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        out = S.sample_lensemble(lam, B, 1 + r, stream=stream)
+        e1.record(stream)
+        S.sync()
+        walls.append(time.perf_counter() - t0)
+        evs.append(e0.elapsed_time(e1))
+    n = out["n"].double()
+    S.close()
+    ms = 1e3 * float(np.median(walls))
+    flops = float((L * n * (n + 1)).sum())  # the paper's 2Lk per step, summed over each chain
+    return {"workload": f"L-ensemble, L={L} items, D={D} features x quality (alpha={alpha}), rank-{D} "
+                        f"eigenbasis, B={B}", "samples_per_s": B / (ms / 1e3), "ms_per_call": ms,
+            "event_ms_per_call": float(np.median(evs)), "mean_kept": float(n.mean()),
+            "max_kept": int(n.max()), "expected_kept": float((lam / (lam + 1)).sum()),
+            "algorithmic_tflops": flops / (ms / 1e3) / 1e12}
+
+
 def bench_serving(args, flags):
     """Poisson stream of projection-DPP requests (U = top-N left singular vectors of L
     unit-norm Gaussian features of dimension D; L log-uniform [500, 20000], D in [64, 512],
@@ -341,6 +382,7 @@ def main():
     ap.add_argument("--marginal-steps", type=int, default=128)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-reweight", action="store_true")
+    ap.add_argument("--no-lensemble", action="store_true")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=300.0, help="serving arrivals per second")
@@ -533,6 +575,8 @@ def main():
     if not args.no_reweight and rank == 0:
         out["reweight"] = bench_reweight(x, spec, stream)
     S.close()
+    if not args.no_lensemble and rank == 0:
+        out["lensemble"] = bench_lensemble(flags, stream)
     if not args.no_batching and rank == 0:
         out["batching"] = bench_batching(args, flags, stream)
     if not args.no_serving and rank == 0:

@@ -201,6 +201,36 @@ int ffs_sample_noalloc(const void* U, int dtype, int64_t L, int64_t N, int64_t B
                        int32_t* out_x, void* cuda_stream);
 
 /*
+ * ffs_sample_lensemble - draw B samples of the L-ensemble DPP whose correlation matrix is
+ * C = sum_j lambda_j u_j u_j^dagger (main text, text-summarisation example): each
+ * eigenvector u_j (column j of the handle's U, so U holds the eigenvectors of C with
+ * nonzero eigenvalue, orthonormal) is kept with probability lambda_j / (lambda_j + 1),
+ * and the kept columns form the U of Eq. 1, sampled by the chain rule with N = the
+ * number kept.  Sample b is keyed like ffs_sample_ex; its keep decision for column j
+ * uses Philox stream 2, block j (a 53-bit uniform built like the site uniforms; kept
+ * when it is below lambda_j / (lambda_j + 1), never when lambda_j <= 0).  The kept
+ * columns in ascending order are then shuffled by the stream-0 Fisher-Yates shuffle
+ * over their count.  All samples advance together for as many steps as the longest
+ * chain; shorter chains stop early.
+ *   lambda     host or device, N eigenvalues (a non-finite value is FFS_E_ARG).
+ *   out_x      device, B x N int32: the n_b sites of sample b in draw order, then -1.
+ *   out_n      device, B int32, or NULL: n_b, the number of kept eigenvectors.
+ *   out_perm   device, B x N int32, or NULL: the kept columns in the order the chain
+ *              used them, then the other columns ascending.
+ *   out_logp   device, B doubles, or NULL: log of the chain's probability of x given
+ *              the kept columns and their order (0 for an empty sample).
+ *   force_x    device, B x N int32, or NULL: teacher forcing of the first n_b entries.
+ *   out_probs  device, B x N x L float, or NULL: the normalised conditionals (zero rows
+ *              past n_b).
+ * Needs a handle in the batched form with the blocked state (the default flags), else
+ * FFS_E_UNSUPPORTED.  The call reads the longest chain length back to the host
+ * (it synchronises cuda_stream once, before the sampling launches).
+ */
+int ffs_sample_lensemble(ffs_handle h, const double* lambda, int64_t B, uint64_t seed,
+                         uint64_t first_sample_index, int32_t* out_x, int32_t* out_n, int32_t* out_perm,
+                         double* out_logp, const int32_t* force_x, float* out_probs, void* cuda_stream);
+
+/*
  * ffs_sample_batched - sample many independent instances together (the batching
  * pattern: many U of uneven L and N).  Instance i draws Bs[i] samples of handle hs[i]
  * with seed seeds[i] (sample indices 0..Bs[i]-1) into the device buffer outs[i]

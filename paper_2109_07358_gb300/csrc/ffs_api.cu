@@ -167,6 +167,7 @@ static void release(ffs_ctx* c) {
   cudaFree(c->Ue_tf32);
   cudaFree(c->UT32);
   cudaFree(c->Ust);
+  cudaFree(c->sel_p);
   cudaFree(c->status);
   if (c->status_host) cudaFreeHost(c->status_host);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -368,16 +369,15 @@ int ffs_query(ffs_handle h, int64_t* L, int64_t* N, int* dtype, unsigned* flags,
   return FFS_OK;
 }
 
-int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_index, int64_t n_steps,
-                  int32_t* out_x, int32_t* out_perm, double* out_logp, const int32_t* force_x,
-                  float* out_probs, void* cuda_stream) {
-  if (!h) return fail(nullptr, FFS_E_ARG, "ffs_sample_ex: NULL handle");
-  if (B < 0) return fail(h, FFS_E_ARG, "ffs_sample_ex: B < 0");
-  if (n_steps == 0) n_steps = h->N;
-  if (n_steps < 1 || n_steps > h->N) return fail(h, FFS_E_ARG, "ffs_sample_ex: need 0 <= n_steps <= N");
-  if (B == 0) return FFS_OK;
-  if (!out_x) return fail(h, FFS_E_ARG, "ffs_sample_ex: out_x is NULL");
-  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : h->stream;
+}  // extern "C"
+
+// The sampling loop shared by ffs_sample_ex and ffs_sample_lensemble: waves of samples,
+// each a permutation launch and then n_steps residual + state launches.  Rows of out_x,
+// force_x and out_probs are ldx steps apart.  sel_p / nlen: L-ensemble keep probabilities
+// and per-sample chain lengths (device; null for ordinary calls).
+static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_sample_index, int64_t n_steps,
+                       int64_t ldx, int32_t* out_x, int32_t* out_perm, double* out_logp, const int32_t* force_x,
+                       float* out_probs, cudaStream_t st, const double* sel_p, const int32_t* nlen) {
   const int op = op_mode_of(h->flags);
   const bool plain = op == kOpNone;
 
@@ -391,9 +391,9 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
 
   // Wave size from free device memory.
   size_t per = per_sample_bytes_nc(h, n_steps);
-  if (!x_dev) per += n_steps * 4;
-  if (force_x && !force_dev) per += n_steps * 4;
-  if (out_probs && !probs_dev) per += (size_t)n_steps * h->L * 4;
+  if (!x_dev) per += ldx * 4;
+  if (force_x && !force_dev) per += ldx * 4;
+  if (out_probs && !probs_dev) per += (size_t)ldx * h->L * 4;
   size_t free_b = 0, total_b = 0;
   FFS_CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t reserve = (size_t)512 << 20;
@@ -409,10 +409,10 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
   int32_t* xbuf = nullptr;
   int32_t* fbuf = nullptr;
   float* pbuf = nullptr;
-  if (!x_dev) FFS_CUDA_TRY(h, cudaMallocAsync((void**)&xbuf, (size_t)Bw * n_steps * 4, st));
-  if (force_x && !force_dev) FFS_CUDA_TRY(h, cudaMallocAsync((void**)&fbuf, (size_t)Bw * n_steps * 4, st));
+  if (!x_dev) FFS_CUDA_TRY(h, cudaMallocAsync((void**)&xbuf, (size_t)Bw * ldx * 4, st));
+  if (force_x && !force_dev) FFS_CUDA_TRY(h, cudaMallocAsync((void**)&fbuf, (size_t)Bw * ldx * 4, st));
   if (out_probs && !probs_dev)
-    FFS_CUDA_TRY(h, cudaMallocAsync((void**)&pbuf, (size_t)Bw * n_steps * h->L * 4, st));
+    FFS_CUDA_TRY(h, cudaMallocAsync((void**)&pbuf, (size_t)Bw * ldx * h->L * 4, st));
 
   int rc = FFS_OK;
   for (int64_t b0 = 0; b0 < B && rc == FFS_OK; b0 += Bw) {
@@ -439,14 +439,17 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
     a.P = h->P;
     a.W = h->W;
     a.logp = h->logp;
-    a.x = x_dev ? out_x + b0 * n_steps : xbuf;
-    a.probs = out_probs ? (probs_dev ? out_probs + (size_t)b0 * n_steps * h->L : pbuf) : nullptr;
+    a.x = x_dev ? out_x + b0 * ldx : xbuf;
+    a.probs = out_probs ? (probs_dev ? out_probs + (size_t)b0 * ldx * h->L : pbuf) : nullptr;
     a.status = h->status;
+    a.ldx = ldx;
+    a.sel_p = sel_p;
+    a.nlen = nlen ? nlen + b0 : nullptr;
     if (force_x) {
       if (force_dev) {
-        a.force_x = force_x + b0 * n_steps;
+        a.force_x = force_x + b0 * ldx;
       } else {
-        FFS_CUDA_TRY(h, cudaMemcpyAsync(fbuf, force_x + b0 * n_steps, (size_t)bw * n_steps * 4,
+        FFS_CUDA_TRY(h, cudaMemcpyAsync(fbuf, force_x + b0 * ldx, (size_t)bw * ldx * 4,
                                         cudaMemcpyHostToDevice, st));
         a.force_x = fbuf;
       }
@@ -483,15 +486,15 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
       }
     }
     if (!x_dev)
-      FFS_CUDA_TRY(h, cudaMemcpyAsync(out_x + b0 * n_steps, xbuf, (size_t)bw * n_steps * 4,
+      FFS_CUDA_TRY(h, cudaMemcpyAsync(out_x + b0 * ldx, xbuf, (size_t)bw * ldx * 4,
                                       cudaMemcpyDeviceToHost, st));
     if (out_perm)
       FFS_CUDA_TRY(h, cudaMemcpyAsync(out_perm + b0 * h->N, h->m, (size_t)bw * h->N * 4, cudaMemcpyDefault, st));
     if (out_logp)
       FFS_CUDA_TRY(h, cudaMemcpyAsync(out_logp + b0, h->logp, (size_t)bw * 8, cudaMemcpyDefault, st));
     if (out_probs && !probs_dev)
-      FFS_CUDA_TRY(h, cudaMemcpyAsync(out_probs + (size_t)b0 * n_steps * h->L, pbuf,
-                                      (size_t)bw * n_steps * h->L * 4, cudaMemcpyDeviceToHost, st));
+      FFS_CUDA_TRY(h, cudaMemcpyAsync(out_probs + (size_t)b0 * ldx * h->L, pbuf,
+                                      (size_t)bw * ldx * h->L * 4, cudaMemcpyDeviceToHost, st));
     if (any_host) FFS_CUDA_TRY(h, cudaStreamSynchronize(st));
   }
   if (xbuf) cudaFreeAsync(xbuf, st);
@@ -503,9 +506,88 @@ int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_
     if (*h->status_host != 0) {
       const int code = *h->status_host;
       cudaMemset(h->status, 0, sizeof(int));
-      return fail(h, code, "ffs_sample_ex: device reported an error (see ffs.h status codes)");
+      return fail(h, code, "device reported an error (see ffs.h status codes)");
     }
   }
+  return rc;
+}
+
+extern "C" {
+
+int ffs_sample_ex(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_index, int64_t n_steps,
+                  int32_t* out_x, int32_t* out_perm, double* out_logp, const int32_t* force_x,
+                  float* out_probs, void* cuda_stream) {
+  if (!h) return fail(nullptr, FFS_E_ARG, "ffs_sample_ex: NULL handle");
+  if (B < 0) return fail(h, FFS_E_ARG, "ffs_sample_ex: B < 0");
+  if (n_steps == 0) n_steps = h->N;
+  if (n_steps < 1 || n_steps > h->N) return fail(h, FFS_E_ARG, "ffs_sample_ex: need 0 <= n_steps <= N");
+  if (B == 0) return FFS_OK;
+  if (!out_x) return fail(h, FFS_E_ARG, "ffs_sample_ex: out_x is NULL");
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : h->stream;
+  return sample_core(h, B, seed, first_sample_index, n_steps, n_steps, out_x, out_perm, out_logp, force_x,
+                     out_probs, st, nullptr, nullptr);
+}
+
+int ffs_sample_lensemble(ffs_handle h, const double* lambda, int64_t B, uint64_t seed,
+                         uint64_t first_sample_index, int32_t* out_x, int32_t* out_n, int32_t* out_perm,
+                         double* out_logp, const int32_t* force_x, float* out_probs, void* cuda_stream) {
+  if (!h) return fail(nullptr, FFS_E_ARG, "ffs_sample_lensemble: NULL handle");
+  if (B < 0) return fail(h, FFS_E_ARG, "ffs_sample_lensemble: B < 0");
+  if (B == 0) return FFS_OK;
+  if (!lambda || !out_x) return fail(h, FFS_E_ARG, "ffs_sample_lensemble: lambda and out_x are required");
+  if (!blocked(h) || op_mode_of(h->flags) == kOpNone)
+    return fail(h, FFS_E_UNSUPPORTED, "ffs_sample_lensemble: needs the batched form with the blocked state");
+  for (const void* p : {(const void*)out_x, (const void*)out_n, (const void*)out_perm, (const void*)out_logp,
+                        (const void*)force_x, (const void*)out_probs})
+    if (p && !is_device_ptr(p))
+      return fail(h, FFS_E_ARG, "ffs_sample_lensemble: out_x, out_n, out_perm, out_logp, force_x and "
+                                "out_probs must be device memory");
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : h->stream;
+  const int64_t N = h->N;
+  if (!h->sel_p) FFS_CUDA_TRY(h, cudaMalloc((void**)&h->sel_p, (size_t)N * sizeof(double)));
+  if (is_device_ptr(lambda)) {
+    FFS_CUDA_TRY(h, launch_keep_prob(lambda, N, h->sel_p, h->status, st));
+  } else {
+    FFS_CUDA_TRY(h, cudaMemcpyAsync(h->sel_p, lambda, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, st));
+    FFS_CUDA_TRY(h, launch_keep_prob(h->sel_p, N, h->sel_p, h->status, st));  // in place, per entry
+  }
+  // chain lengths of all samples, and the longest (the number of steps the call runs)
+  int32_t* nlen = out_n;
+  int* dmax = nullptr;
+  if (!nlen) FFS_CUDA_TRY(h, cudaMallocAsync((void**)&nlen, (size_t)B * 4, st));
+  FFS_CUDA_TRY(h, cudaMallocAsync((void**)&dmax, sizeof(int), st));
+  FFS_CUDA_TRY(h, cudaMemsetAsync(dmax, 0, sizeof(int), st));
+  StepArgs a{};
+  a.N = N;
+  a.seed = seed;
+  a.first = first_sample_index;
+  a.sel_p = h->sel_p;
+  FFS_CUDA_TRY(h, launch_lens_count(a, B, nlen, dmax, st));
+  FFS_CUDA_TRY(h, cudaMemcpyAsync(h->status_host, dmax, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FFS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  const int64_t longest = *h->status_host;
+  FFS_CUDA_TRY(h, cudaMemcpy(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (*h->status_host != 0) {
+    cudaMemset(h->status, 0, sizeof(int));
+    if (!out_n) cudaFreeAsync(nlen, st);
+    cudaFreeAsync(dmax, st);
+    return fail(h, FFS_E_ARG, "ffs_sample_lensemble: an eigenvalue is not finite");
+  }
+  // positions past a sample's chain: site -1, conditional 0
+  FFS_CUDA_TRY(h, cudaMemsetAsync(out_x, 0xff, (size_t)B * N * 4, st));
+  if (out_probs) FFS_CUDA_TRY(h, cudaMemsetAsync(out_probs, 0, (size_t)B * N * h->L * 4, st));
+  if (out_logp) FFS_CUDA_TRY(h, cudaMemsetAsync(out_logp, 0, (size_t)B * 8, st));
+  int rc = FFS_OK;
+  if (longest > 0) {
+    rc = sample_core(h, B, seed, first_sample_index, longest, N, out_x, out_perm, out_logp, force_x, out_probs,
+                     st, h->sel_p, nlen);
+  } else if (out_perm) {  // nothing kept anywhere: the column orders are the columns in order
+    a.bw = B;
+    a.m = out_perm;
+    FFS_CUDA_TRY(h, launch_perm_init(a, kOpNone, st));
+  }
+  if (!out_n) cudaFreeAsync(nlen, st);
+  cudaFreeAsync(dmax, st);
   return rc;
 }
 

@@ -114,14 +114,14 @@ __device__ __forceinline__ void draw_outputs(const StepArgs& a, int64_t b, int64
                                              const float* __restrict__ prow) {
   const int tid = threadIdx.x;
   if (tid == 0) {
-    a.x[b * a.n_steps + k] = x;
+    a.x[b * a.ldx + k] = x;
     a.mask[b * a.ldMask + (x >> 5)] |= 1u << (x & 31);
     const double px = (double)prow[x];
     a.logp[b] += (px > 0.0 && Z > 0.0) ? log(px / Z) : -INFINITY;
     if (!(Z > 0.0) || !isfinite(Z)) set_status(a.status, FFS_E_NUMERIC);
   }
   if (a.probs) {
-    float* pr = a.probs + ((size_t)b * a.n_steps + k) * a.L;
+    float* pr = a.probs + ((size_t)b * a.ldx + k) * a.L;
     const double iz = Z > 0.0 ? 1.0 / Z : 0.0;
     for (int64_t i = tid; i < a.L; i += blockDim.x) pr[i] = (float)((double)prow[i] * iz);
   }
@@ -129,7 +129,7 @@ __device__ __forceinline__ void draw_outputs(const StepArgs& a, int64_t b, int64
 
 __device__ __forceinline__ int forced_site(const StepArgs& a, int64_t b, int64_t k) {
   if (!a.force_x) return -1;
-  const int f = a.force_x[b * a.n_steps + k];
+  const int f = a.force_x[b * a.ldx + k];
   return (f < 0 || f >= a.L) ? -2 : f;
 }
 

@@ -66,6 +66,9 @@ void fill_inst(GroupInst& g, ffs_ctx* c, int64_t B, uint64_t seed, uint64_t firs
   a.force_x = nullptr;
   a.probs = nullptr;
   a.status = c->status;
+  a.ldx = n_steps;
+  a.sel_p = nullptr;
+  a.nlen = nullptr;
   BlockedArgs& t = g.t;
   t.Nc = n_steps;
   t.W = c->W;

@@ -113,7 +113,7 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-enum { kStreamPerm = 0, kStreamSite = 1 };
+enum { kStreamPerm = 0, kStreamSite = 1, kStreamSelect = 2 };
 
 __host__ __device__ __forceinline__ uint4 philox_block(uint64_t seed, uint32_t block, uint32_t stream,
                                                        uint64_t sample) {
@@ -124,6 +124,14 @@ __host__ __device__ __forceinline__ uint4 philox_block(uint64_t seed, uint32_t b
 // 53-bit uniform in [0, 1) of step k.
 __host__ __device__ __forceinline__ double site_uniform(uint64_t seed, uint64_t sample, int k) {
   const uint4 w = philox_block(seed, (uint32_t)k, kStreamSite, sample);
+  const uint64_t bits = ((uint64_t)(w.x >> 5) << 26) | (uint64_t)(w.y >> 6);
+  return (double)bits * 0x1p-53;
+}
+
+// Uniform in [0, 1) that decides whether eigenvector j of an L-ensemble is kept
+// (stream 2, block j; built like the site uniforms).
+__host__ __device__ __forceinline__ double select_uniform(uint64_t seed, uint64_t sample, int64_t j) {
+  const uint4 w = philox_block(seed, (uint32_t)j, kStreamSelect, sample);
   const uint64_t bits = ((uint64_t)(w.x >> 5) << 26) | (uint64_t)(w.y >> 6);
   return (double)bits * 0x1p-53;
 }
@@ -183,6 +191,7 @@ struct ffs_ctx {
   int tm_U_ready = -1;   // operand mode * 1000 + column tile that tmU was encoded for
   int res_bn = 0;        // residual column tile in use (0: not chosen yet)
   int64_t tm_H_B = -1;   // workspace capacity tmH was encoded for
+  double* sel_p = nullptr;       // N keep probabilities lambda / (lambda + 1) (L-ensemble calls)
   int* status = nullptr;         // device status word
   int* status_host = nullptr;    // pinned mirror
 

@@ -77,11 +77,29 @@ __device__ __forceinline__ void put_operand(const StepArgs& a, int op, int64_t b
 // One thread per sample: Fisher-Yates over (0..N-1) driven by Philox stream 0 (block j
 // serves shuffle steps N-1-2j and N-2-2j, 64 bits each, index = mulhi(r, i+1)).  Also
 // writes the step-0 operand h = e_{m_0} (the operand buffer is zeroed beforehand).
+// L-ensemble (sel_p set): column j is kept when its stream-2 uniform is below sel_p[j];
+// the kept columns, ascending, are shuffled the same way over their count n, and the
+// others follow in ascending order (the chain never reaches them).
+__device__ __forceinline__ bool kept_column(const StepArgs& a, uint64_t sample, int64_t j) {
+  return select_uniform(a.seed, sample, j) < a.sel_p[j];
+}
+
 __device__ __forceinline__ void perm_one(const StepArgs& a, int op_mode, int64_t b) {
   const uint64_t sample = a.first + (uint64_t)b;
   int32_t* m = const_cast<int32_t*>(a.m) + b * a.N;
-  for (int64_t i = 0; i < a.N; ++i) m[i] = (int32_t)i;
-  int64_t i = a.N - 1;
+  int64_t n = a.N;
+  if (a.sel_p) {
+    n = 0;
+    for (int64_t j = 0; j < a.N; ++j)
+      if (kept_column(a, sample, j)) m[n++] = (int32_t)j;
+    int64_t r = n;
+    for (int64_t j = 0; j < a.N; ++j)
+      if (!kept_column(a, sample, j)) m[r++] = (int32_t)j;
+    if (n == 0) return;
+  } else {
+    for (int64_t i = 0; i < a.N; ++i) m[i] = (int32_t)i;
+  }
+  int64_t i = n - 1;
   uint32_t block = 0;
   while (i >= 1) {
     const uint4 w = philox_block(a.seed, block, kStreamPerm, sample);
@@ -109,6 +127,38 @@ __device__ __forceinline__ void perm_one(const StepArgs& a, int op_mode, int64_t
     else
       put_operand(a, op_mode, b, m[0], 1.0);
   }
+}
+
+// L-ensemble: the chain length of every sample (the number of kept columns) and its
+// maximum over the call.
+__global__ void lens_count_kernel(StepArgs a, int64_t B, int32_t* nlen, int* max_len) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int n = 0;
+  for (int64_t j = 0; j < a.N; ++j) n += kept_column(a, a.first + (uint64_t)b, j) ? 1 : 0;
+  nlen[b] = n;
+  atomicMax(max_len, n);
+}
+
+// Keep probabilities lambda / (lambda + 1) (lambda <= 0: never kept); a non-finite
+// lambda is an argument error.
+__global__ void keep_prob_kernel(const double* lambda, int64_t N, double* p, int* status) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const double l = lambda[j];
+  if (!isfinite(l)) set_status(status, FFS_E_ARG);
+  p[j] = (l > 0.0 && isfinite(l)) ? l / (l + 1.0) : 0.0;
+}
+
+cudaError_t launch_lens_count(const StepArgs& a, int64_t B, int32_t* nlen, int* max_len, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  lens_count_kernel<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(a, B, nlen, max_len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keep_prob(const double* lambda, int64_t N, double* p, int* status, cudaStream_t s) {
+  keep_prob_kernel<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(lambda, N, p, status);
+  return cudaGetLastError();
 }
 
 __global__ void perm_init_kernel(StepArgs a, int op_mode) {

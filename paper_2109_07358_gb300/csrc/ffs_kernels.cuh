@@ -30,10 +30,14 @@ struct StepArgs {
   float* P;                // bw x ldP
   void* W;                 // bw x N x N state
   double* logp;            // bw
-  int32_t* x;              // bw x n_steps
-  const int32_t* force_x;  // bw x n_steps or null
-  float* probs;            // bw x n_steps x L or null
+  int32_t* x;              // bw x ldx
+  const int32_t* force_x;  // bw x ldx or null
+  float* probs;            // bw x ldx x L or null
   int* status;
+  int64_t ldx;             // row stride of x / force_x / probs in steps: n_steps, or N when
+                           // samples have their own chain lengths
+  const double* sel_p;     // L-ensemble: N keep probabilities of the columns, or null
+  const int32_t* nlen;     // bw per-sample chain lengths (<= n_steps), or null: all n_steps
 };
 
 // Precision of the per-sample elimination state.
@@ -59,6 +63,10 @@ int blocked_step_samples_per_cta();
 cudaError_t configure_blocked();
 
 cudaError_t launch_perm_init(const StepArgs& a, int op_mode, cudaStream_t s);
+// L-ensemble set-up: keep probabilities from the eigenvalues, then the per-sample chain
+// lengths of samples first .. first + B - 1 (a.seed, a.first, a.N, a.sel_p) and their max.
+cudaError_t launch_keep_prob(const double* lambda, int64_t N, double* p, int* status, cudaStream_t s);
+cudaError_t launch_lens_count(const StepArgs& a, int64_t B, int32_t* nlen, int* max_len, cudaStream_t s);
 cudaError_t launch_ortho_check(const void* U64, bool cplx, int64_t L, int64_t N, double* maxdev,
                                cudaStream_t s);
 cudaError_t launch_derive_operands(ffs_ctx* c, cudaStream_t s);

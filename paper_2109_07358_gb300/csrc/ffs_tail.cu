@@ -174,6 +174,15 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
   const int lane = threadIdx.x & 31;
   const int64_t L = a.L, N = a.N, Nc = t.Nc;
   const float* __restrict__ prow = a.P + b * a.ldP;
+  const int64_t len = a.nlen ? (int64_t)a.nlen[b] : a.n_steps;  // this sample's chain length
+  if (k >= len) {  // the chain has ended (an L-ensemble sample that kept fewer columns)
+    if (lane == 0) a.x[b * a.ldx + k] = -1;
+    if (a.probs) {
+      float* pr = a.probs + ((size_t)b * a.ldx + k) * L;
+      for (int64_t y = lane; y < L; y += 32) pr[y] = 0.f;
+    }
+    return;
+  }
 
   // draw: Z over 128-site chunks, then the first chunk whose running sum passes t
   const int64_t nch = (L + 127) / 128;
@@ -200,18 +209,18 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
     }
   }
   if (lane == 0) {
-    a.x[b * a.n_steps + k] = x;
+    a.x[b * a.ldx + k] = x;
     a.mask[b * a.ldMask + (x >> 5)] |= 1u << (x & 31);
     const double px = (double)prow[x];
     a.logp[b] += (px > 0.0 && Z > 0.0) ? log(px / Z) : -INFINITY;
     if (!(Z > 0.0) || !isfinite(Z)) set_status(a.status, FFS_E_NUMERIC);
   }
   if (a.probs) {
-    float* pr = a.probs + ((size_t)b * a.n_steps + k) * L;
+    float* pr = a.probs + ((size_t)b * a.ldx + k) * L;
     const double iz = Z > 0.0 ? 1.0 / Z : 0.0;
     for (int64_t y = lane; y < L; y += 32) pr[y] = (float)((double)prow[y] * iz);
   }
-  if (k + 1 >= a.n_steps) return;
+  if (k + 1 >= len) return;
 
   const int64_t k0 = (k / NB) * NB, i = k - k0, k1 = min(k0 + NB, Nc);
   const int64_t ldw = Nc;  // the state keeps Nc x Nc entries per sample
@@ -317,10 +326,11 @@ __device__ __forceinline__ void panel_s_body(const StepArgs& a, const BlockedArg
   const int tid = threadIdx.x;
   const int64_t N = a.N;
   const int nbr = (int)(k1 - k0);
+  if (a.nlen && a.nlen[b] <= k1) return;  // chain ends in this panel (uniform over the CTA)
   const int32_t* mrow = a.m + b * N;
   const A* Us = (const A*)a.Ust;  // U in the state type
   const A* W0P = (const A*)t.W0P + (size_t)b * t.Nc * NB;
-  if (tid < NB) xs[tid] = tid < nbr ? a.x[b * a.n_steps + k0 + tid] : 0;
+  if (tid < NB) xs[tid] = tid < nbr ? a.x[b * a.ldx + k0 + tid] : 0;
   __syncthreads();
   // thread owns entries (ii, cc) = (tid / 32 + 8 q, tid % 32)
   const int cc = tid & 31, r0 = tid >> 5;
@@ -397,6 +407,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t N = a.N, Nc = t.Nc;
   const int nbr = (int)(k1 - k0);
+  if (a.nlen && a.nlen[b] <= k1) return;  // chain ends in this panel (uniform over the CTA)
   const int64_t c0 = k1 + cb * 32;
   const int64_t c = c0 + lane;
   const bool cval = c < Nc;
@@ -407,7 +418,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   const A* Us = (const A*)a.Ust;  // U in the state type
 
   for (int e = tid; e < NB * NB; e += blockDim.x) Si[e] = ((const A*)t.Sinv)[(size_t)b * NB * NB + e];
-  if (tid < NB) xs[tid] = tid < nbr ? a.x[b * a.n_steps + k0 + tid] : 0;
+  if (tid < NB) xs[tid] = tid < nbr ? a.x[b * a.ldx + k0 + tid] : 0;
   __syncthreads();
 
   // Y = U[x_new, m_T] - U[x_new, m_<k0] W0_T; thread owns rows warp + 8q, column lane

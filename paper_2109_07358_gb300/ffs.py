@@ -82,11 +82,13 @@ def lib() -> ctypes.CDLL:
         L.ffs_server_destroy.restype = None
         L.ffs_profile.argtypes = [vp, i32]
         L.ffs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]
+        L.ffs_sample_lensemble.argtypes = [vp, vp, i64, u64, u64, vp, vp, vp, vp, vp, vp, vp]
         L.ffs_jastrow_estimate.argtypes = [vp, i64, i64, i64, ctypes.POINTER(ffs_csr), vp, ctypes.POINTER(ffs_csr),
                                            vp, vp, vp, vp]
         for name in ("ffs_create", "ffs_create_ex", "ffs_sample", "ffs_sample_ex", "ffs_sync", "ffs_query",
                      "ffs_profile", "ffs_profile_read", "ffs_sample_noalloc", "ffs_sample_batched",
-                     "ffs_server_create", "ffs_submit", "ffs_wait", "ffs_server_stats", "ffs_jastrow_estimate"):
+                     "ffs_server_create", "ffs_submit", "ffs_wait", "ffs_server_stats", "ffs_jastrow_estimate",
+                     "ffs_sample_lensemble"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -138,6 +140,13 @@ def ffs_sample_ex(h, B: int, seed: int, first_sample_index: int, n_steps: int, o
                   out_logp=None, force_x=None, out_probs=None, stream=None):
     _check(lib().ffs_sample_ex(h, B, seed, first_sample_index, n_steps, _ptr(out_x), _ptr(out_perm),
                                _ptr(out_logp), _ptr(force_x), _ptr(out_probs), _stream(stream)), h)
+
+
+def ffs_sample_lensemble(h, lam, B: int, seed: int, first_sample_index: int, out_x, out_n=None, out_perm=None,
+                         out_logp=None, force_x=None, out_probs=None, stream=None):
+    _check(lib().ffs_sample_lensemble(h, _ptr(lam), B, seed, first_sample_index, _ptr(out_x), _ptr(out_n),
+                                      _ptr(out_perm), _ptr(out_logp), _ptr(force_x), _ptr(out_probs),
+                                      _stream(stream)), h)
 
 
 def ffs_sample_noalloc(U, dtype: int, L: int, N: int, B: int, seed: int, out_x, stream=None):
@@ -271,6 +280,27 @@ class Sampler:
         pr = torch.empty((B, K, self.L), dtype=torch.float32, device=device) if probs else None
         ffs_sample_ex(self.h, B, seed, first_sample_index, n_steps, x, pm, lp, force_x, pr, stream)
         res = {"x": x}
+        if perm:
+            res["perm"] = pm
+        if logp:
+            res["logp"] = lp
+        if probs:
+            res["probs"] = pr
+        return res
+
+    def sample_lensemble(self, lam, B: int, seed: int = 0, first_sample_index: int = 0, perm=False, logp=False,
+                         force_x=None, probs=False, stream=None, device="cuda"):
+        """L-ensemble draws with eigenvalues lam (one per column of U): dict with 'x' (B x N,
+        -1 past each sample's n_b), 'n' (B), and the optional outputs."""
+        import torch
+
+        x = torch.empty((B, self.N), dtype=torch.int32, device=device)
+        n = torch.empty((B,), dtype=torch.int32, device=device)
+        pm = torch.empty((B, self.N), dtype=torch.int32, device=device) if perm else None
+        lp = torch.empty((B,), dtype=torch.float64, device=device) if logp else None
+        pr = torch.empty((B, self.N, self.L), dtype=torch.float32, device=device) if probs else None
+        ffs_sample_lensemble(self.h, lam, B, seed, first_sample_index, x, n, pm, lp, force_x, pr, stream)
+        res = {"x": x, "n": n}
         if perm:
             res["perm"] = pm
         if logp:

@@ -1,0 +1,191 @@
+"""L-ensemble DPP sampling on the GPU (ffs_sample_lensemble) against the oracle.
+
+* Keep decisions, chain lengths and column orders: bit-exact against the oracle.
+* Teacher-forced conditionals within the mode's tolerance (1e-6 FP32 path, 1e-4 the
+  chosen BF16x3 form), zero past each chain; free-running draws identical except at
+  excused CDF boundaries; log-probabilities.
+* Chains of uneven length that end inside and across 32-column panels (real and
+  complex U), samples that keep nothing, all-kept (bit-identical to ffs_sample_ex),
+  sharding by first_sample_index, and argument errors.
+* Distribution: 2 x 10^5 GPU samples of a 6-item kernel against P(S) = det(C_S)/det(C+I)
+  over all subsets (chi-squared).
+"""
+from collections import Counter
+
+import numpy as np
+import pytest
+import torch
+from scipy.stats import chisquare
+
+from oracle import ffs_oracle as orc
+from paper_2109_07358_gb300 import ffs
+from paper_2109_07358_gb300 import workloads as w
+from tests.parity_util import excused
+
+pytestmark = pytest.mark.gpu
+
+FP32 = ffs.FFS_RES_FP32 | ffs.FFS_STATE_FP64
+CHOSEN = ffs.FFS_RES_BF16X3 | ffs.FFS_STATE_DF64
+SEED = 777
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2109_07358_gb300.build import build
+
+    build()
+    assert torch.cuda.is_available()
+
+
+def kernel_case(name):
+    if name == "features":   # quality-scaled Gaussian features: a spread spectrum
+        lam, V = w.lensemble_spectrum(w.lensemble_quality_features(300, 40, 0.5, seed=4))
+        return V, lam
+    if name == "panels_real":   # lambda = 1: chains of 64 +- 6 steps cross the 64 boundary
+        return w.haar(256, 128, seed=5, complex_=False), np.ones(128)
+    if name == "panels_complex":
+        return w.haar(160, 90, seed=6), np.full(90, 1.5)
+    raise KeyError(name)
+
+
+def sampler(V, flags):
+    return ffs.Sampler(torch.from_numpy(np.ascontiguousarray(V)).cuda(), flags)
+
+
+_RECS = {}
+
+
+def oracle(case, V, lam, B):
+    if case not in _RECS:
+        _RECS[case] = [orc.lensemble_sample_one(V, lam, SEED, s, record=True) for s in range(B)]
+    return _RECS[case]
+
+
+@pytest.mark.parametrize("case", ["features", "panels_real", "panels_complex"])
+@pytest.mark.parametrize("mode,tol", [("fp32", 1e-6), ("chosen", 1e-4)])
+def test_parity(case, mode, tol):
+    V, lam = kernel_case(case)
+    N = V.shape[1]
+    B = 70
+    recs = oracle(case, V, lam, B)
+    S = sampler(V, FP32 if mode == "fp32" else CHOSEN)
+    out = S.sample_lensemble(torch.from_numpy(lam).cuda(), B, SEED, perm=True, logp=True)
+    S.sync()
+    X, n, P = out["x"].cpu().numpy(), out["n"].cpu().numpy(), out["perm"].cpu().numpy()
+    for b, r in enumerate(recs):
+        nb = r["kept"].size
+        assert n[b] == nb
+        assert np.array_equal(P[b, :nb], r["m_full"])
+        assert np.array_equal(P[b, nb:], np.setdiff1d(np.arange(N), r["kept"]))
+        assert np.all(X[b, nb:] == -1)
+    # free-running draws: identical up to excused boundary cases
+    bad = []
+    same = 0
+    for b, r in enumerate(recs):
+        d = np.nonzero(X[b, :n[b]] != r["x"])[0]
+        if d.size == 0:
+            same += 1
+        elif not excused(r, int(d[0]), X[b, d[0]], tol):
+            bad.append((b, int(d[0])))
+    assert not bad, bad
+    assert same >= 0.95 * B
+    # teacher forcing on the oracle's draws: conditionals, zero rows past each chain
+    force = np.full((B, N), -1, dtype=np.int32)
+    for b, r in enumerate(recs):
+        force[b, :r["x"].size] = r["x"]
+    outf = S.sample_lensemble(torch.from_numpy(lam).cuda(), B, SEED, logp=True,
+                              force_x=torch.from_numpy(force).cuda(), probs=True)
+    S.sync()
+    Pr = outf["probs"].cpu().double().numpy()
+    lp = outf["logp"].cpu().numpy()
+    err = 0.0
+    for b, r in enumerate(recs):
+        nb = r["kept"].size
+        if nb:
+            err = max(err, float(np.abs(Pr[b, :nb] - r["probs"]).max()))
+            assert abs(lp[b] - r["logp"]) <= 1e-3 * max(1.0, abs(r["logp"]))
+        assert not Pr[b, nb:].any()
+    S.close()
+    print(f"L-ensemble {case} {mode}: max |dP| {err:.2e}, chain lengths {n.min()}..{n.max()}, "
+          f"identical samples {same}/{B}")
+    assert err <= tol
+
+
+def test_all_kept_equals_plain_sampling():
+    V = w.haar(200, 48, seed=7)
+    S = sampler(V, CHOSEN)
+    a = S.sample_lensemble(np.full(48, 1e20), 100, SEED, perm=True, logp=True)
+    b = S.sample(100, SEED, perm=True, logp=True)
+    S.sync()
+    assert torch.equal(a["x"], b["x"]) and torch.equal(a["perm"], b["perm"])
+    assert torch.equal(a["logp"], b["logp"])
+    assert bool((a["n"] == 48).all())
+    S.close()
+
+
+def test_nothing_kept_and_mixed():
+    V = w.haar(64, 10, seed=8, complex_=False)
+    S = sampler(V, CHOSEN)
+    a = S.sample_lensemble(np.zeros(10), 33, SEED, perm=True, logp=True)
+    S.sync()
+    assert bool((a["x"] == -1).all()) and bool((a["n"] == 0).all()) and bool((a["logp"] == 0).all())
+    assert torch.equal(a["perm"].cpu(), torch.arange(10, dtype=torch.int32).repeat(33, 1))
+    lam = np.array([0.0, 1e20, 0.0, 0.3, 1e20, 0.0, 2.0, 0.0, 0.0, 1e20])
+    c = S.sample_lensemble(lam, 50, SEED, perm=True)
+    S.sync()
+    for s in range(50):
+        r = orc.lensemble_sample_one(V, lam, SEED, s)
+        nb = r["kept"].size
+        assert int(c["n"][s]) == nb and {1, 4, 9} <= set(r["kept"].tolist())
+        assert np.array_equal(c["x"][s, :nb].cpu().numpy(), r["x"])
+    S.close()
+
+
+def test_sharding_by_sample_index():
+    V, lam = kernel_case("features")
+    S = sampler(V, CHOSEN)
+    lam_d = torch.from_numpy(lam).cuda()
+    whole = S.sample_lensemble(lam_d, 96, SEED)
+    a = S.sample_lensemble(lam_d, 40, SEED)
+    b = S.sample_lensemble(lam_d, 56, SEED, first_sample_index=40)
+    S.sync()
+    assert torch.equal(whole["x"], torch.cat([a["x"], b["x"]]))
+    assert torch.equal(whole["n"], torch.cat([a["n"], b["n"]]))
+    S.close()
+
+
+def test_argument_errors():
+    V = w.haar(64, 10, seed=8, complex_=False)
+    S = sampler(V, CHOSEN)
+    lam = np.ones(10)
+    lam[3] = np.nan
+    with pytest.raises(ffs.FFSError) as e:
+        S.sample_lensemble(lam, 4, SEED)
+    assert e.value.code == ffs.FFS_E_ARG
+    S.close()
+    for flags in (ffs.FFS_FORM_PLAIN, ffs.FFS_RES_FP32 | ffs.FFS_STATE_FP64 | ffs.FFS_TAIL_UNBLOCKED):
+        S = sampler(V, flags)
+        with pytest.raises(ffs.FFSError) as e:
+            S.sample_lensemble(np.ones(10), 4, SEED)
+        assert e.value.code == ffs.FFS_E_UNSUPPORTED
+        S.close()
+
+
+def test_distribution_brute_force():
+    Phi = w.lensemble_quality_features(6, 4, 0.9, seed=3)
+    lam, V = w.lensemble_spectrum(Phi)
+    P = orc.lensemble_set_probabilities(Phi @ Phi.T)
+    B = 200_000
+    S = sampler(V, CHOSEN)
+    out = S.sample_lensemble(lam, B, 0)
+    S.sync()
+    S.close()
+    X = out["x"].cpu().numpy()
+    cnt = Counter(tuple(sorted(int(v) for v in row if v >= 0)) for row in X)
+    keys = [s for s, p in P.items() if p > 1e-12]
+    assert sum(cnt.get(s, 0) for s in keys) == B
+    obs = np.array([cnt.get(s, 0) for s in keys], dtype=float)
+    exp = np.array([P[s] * B for s in keys])
+    p = chisquare(obs, exp * obs.sum() / exp.sum()).pvalue
+    print(f"L-ensemble brute force (6 items, rank 4, {len(keys)} sets): chi-squared p = {p:.3f}")
+    assert p > 0.01
