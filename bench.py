@@ -76,12 +76,62 @@ def flops_per_sample(L, N, cplx):
 
 
 def tail_flops_per_sample(N, cplx):
-    """Arithmetic of the per-sample Gauss-Jordan state update as implemented: at step k
+    """Arithmetic of the per-sample Gauss-Jordan state update (unblocked count): at step k
     (0-based, k < N-1) a k x (N-k) product of the new row with the state and a
     k x (N-k-1) rank-1 update, 2 real flops per real multiply-add (8 per complex)."""
     k = np.arange(N - 1, dtype=np.float64)
     macs = float(np.sum(k * (N - k) + k * (N - k - 1)))
     return macs * (8 if cplx else 2)
+
+
+def blocked_flops_per_sample(N, cplx, nb=32):
+    """Algorithmic flops per sample of each kernel of the blocked state update, as the
+    kernels compute it (2 real flops per real multiply-add, 8 per complex):
+      step     at step k in panel [k0, k1): the new row against the state on the panel
+               columns (k x (k1 - k)) and the rank-1 update (k x (k1 - k - 1));
+      panel_s  per panel with trailing columns: S = D - C W0_P (nb x k0 x nb) and its
+               Gauss-Jordan inverse (nb x nb x 2 nb);
+      panel    per panel, T = [k1, N): Y = U - C W0_T (nb x k0 x |T|), S^-1 Y
+               (nb x nb x |T|), W0_T - W0_P Bot (k0 x nb x |T|)."""
+    f = 8 if cplx else 2
+    step = panel_s = panel = 0.0
+    for k in range(N - 1):
+        k0 = (k // nb) * nb
+        k1 = min(k0 + nb, N)
+        step += k * (k1 - k) + k * (k1 - k - 1)
+    for k0 in range(0, N, nb):
+        k1 = min(k0 + nb, N)
+        if k1 >= N:
+            break
+        T = N - k1
+        panel_s += nb * k0 * nb + nb * nb * 2 * nb
+        panel += T * nb * (2 * k0 + nb)
+    return {"step": step * f, "panel_s": panel_s * f, "panel": panel * f}
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
+# captured launches of one timed step) of the dominant kernel, from one ncu capture of
+# this workload, with the digest of the kernel sources it was taken on: once those
+# sources change the figure is stale and is reported as null.
+NCU_TRAFFIC = {}
+KERNEL_SOURCES = ("ffs_tail.cu", "ffs_arith.cuh", "ffs_kernels.cuh", "ffs_draw.cuh", "ffs_internal.cuh")
+
+
+def kernel_source_digest():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2109_07358_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, args):
+    rec = NCU_TRAFFIC.get((kernel, args.workload, args.chosen, args.state))
+    if rec is None or rec[1] != kernel_source_digest():
+        return None
+    return rec[0]
 
 
 class ClockSampler:
@@ -326,6 +376,44 @@ def bench_lensemble(flags, stream, B=4096, reps=3):
             "algorithmic_tflops": flops / (ms / 1e3) / 1e12}
 
 
+def bench_metropolis(flags, stream, B=4096, reps=3):
+    """Large-L variant (Supplementary Section S-7): open chain of L = 2^20 sites, N = 128,
+    m_cond = 64 Metropolis updates per step; CUDA-event time per call of B samples,
+    median of `reps` after one warm-up, next to one call of the exact all-site path on
+    the same handle."""
+    import torch
+
+    from paper_2109_07358_gb300 import ffs
+    from paper_2109_07358_gb300 import workloads as w
+
+    L, N, M = 1 << 20, 128, 64
+    U = torch.from_numpy(w.open_chain(L, N)).cuda()
+    torch.cuda.synchronize()
+    S = ffs.Sampler(U, flags, stream=stream)
+    x = torch.empty((B, N), dtype=torch.int32, device="cuda")
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        S.sync()
+        return e0.elapsed_time(e1)
+
+    def mcmc(seed):
+        return lambda: ffs.ffs_sample_metropolis(S.h, B, seed, 0, 0, M, x, stream=stream)
+
+    timed(mcmc(0))
+    ms = float(np.median([timed(mcmc(1 + r)) for r in range(reps)]))
+    ffs.ffs_sample_ex(S.h, 64, 0, 0, 0, x[:64], stream=stream)
+    S.sync()
+    ms_exact = timed(lambda: ffs.ffs_sample_ex(S.h, B, 0, 0, 0, x, stream=stream))
+    S.close()
+    return {"workload": f"open chain L={L}, N={N}, m_cond={M}, B={B}", "samples_per_s": B / (ms / 1e3),
+            "ms_per_call": ms, "exact_path_ms_per_call": ms_exact,
+            "exact_path_samples_per_s": B / (ms_exact / 1e3)}
+
+
 def bench_serving(args, flags):
     """Poisson stream of projection-DPP requests (U = top-N left singular vectors of L
     unit-norm Gaussian features of dimension D; L log-uniform [500, 20000], D in [64, 512],
@@ -383,6 +471,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-reweight", action="store_true")
     ap.add_argument("--no-lensemble", action="store_true")
+    ap.add_argument("--no-metropolis", action="store_true")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=300.0, help="serving arrivals per second")
@@ -440,6 +529,7 @@ def main():
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")   # lets a profiler capture the timed steps only
         ev0.record(stream)
         t0 = time.perf_counter()
         for i in range(args.steps):
@@ -447,6 +537,7 @@ def main():
         ev1.record(stream)
         S.sync()
         wall = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
     barrier()
     ms_total = ev0.elapsed_time(ev1)
     prof = ffs.ffs_profile_read(S.h)
@@ -458,14 +549,16 @@ def main():
     ms_step = ms_total / args.steps
     value = world * B / (ms_step / 1e3)
 
-    # per-phase roofline
+    # per-kernel time (CUDA events around every launch on the handle's stream) and roofline
     res_ms, res_n = prof["residual"]
     tail_ms, tail_n = prof["tail"]
     panel_ms, panel_n = prof["panel"]
+    pans_ms, pans_n = prof["panel_s"]
     perm_ms, perm_n = prof["perm"]
-    res_flops = flops_per_sample(L, N, cplx) * B * args.steps
-    issued = 2 * (2 * L) * (2 * N) * N * B * args.steps if cplx else 2 * L * N * N * B * args.steps
-    tail_fl = tail_flops_per_sample(N, cplx) * B * args.steps
+    K = args.steps
+    res_flops = flops_per_sample(L, N, cplx) * B * K
+    issued = 2 * (2 * L) * (2 * N) * N * B * K if cplx else 2 * L * N * N * B * K
+    bf = {k: v * B * K for k, v in blocked_flops_per_sample(N, cplx).items()}
     mult = {"bf16x3": 3, "fp32": 1, "tf32": 1, "bf16": 1}[args.chosen]
     if args.chosen == "fp32":
         res_peak, res_unit, res_bound = NOMINAL_FP32_TFLOPS, "TFLOP/s", "alu"
@@ -473,36 +566,46 @@ def main():
         res_peak, res_unit, res_bound = peaks["bf16_sus"] / 2, "TFLOP/s", "tensor"
     else:
         res_peak, res_unit, res_bound = peaks["bf16_sus"] / mult, "TFLOP/s", "tensor"
+    # a double-float multiply-add takes about 12 FP32-pipe instructions (exact product of
+    # the high parts by FMA, cross terms, error-free sum), so its peak is FP32 / 12
+    st_peak, st_src = {"fp64": (NOMINAL_FP64_TFLOPS, "nominal FP64 rate (1.25 TFLOP/s)"),
+                       "fp32": (NOMINAL_FP32_TFLOPS, "nominal FP32 rate (152 SMs x 128 lanes x 2 x 2.07 GHz)"),
+                       "df64": (NOMINAL_FP32_TFLOPS / 12, "nominal FP32 rate / 12 (FP32-pipe instructions per "
+                                "double-float multiply-add)")}[args.state]
+
+    def tfl(fl, ms):
+        return fl / (ms / 1e3) / 1e12 if ms else None
+
     phases = {
-        "residual": {"ms": res_ms / args.steps, "launches_per_step": res_n / args.steps,
-                     "algorithmic_tflops": res_flops / (res_ms / 1e3) / 1e12 if res_ms else None,
-                     "issued_tflops": issued * mult / (res_ms / 1e3) / 1e12 if res_ms else None},
-        "tail_step": {"ms": tail_ms / args.steps, "launches_per_step": tail_n / args.steps},
-        "tail_panel": {"ms": panel_ms / args.steps, "launches_per_step": panel_n / args.steps},
-        "tail_total": {"ms": (tail_ms + panel_ms) / args.steps,
-                       "state_tflops": tail_fl / ((tail_ms + panel_ms) / 1e3) / 1e12 if tail_ms else None},
-        "perm": {"ms": perm_ms / args.steps, "launches_per_step": perm_n / args.steps},
+        "residual": {"kernel": "residual_tc_kernel" if args.chosen != "fp32" else "residual_fp32_kernel",
+                     "ms": res_ms / K, "launches_per_step": res_n / K,
+                     "algorithmic_tflops": tfl(res_flops, res_ms), "issued_tflops": tfl(issued * mult, res_ms)},
+        "tail_step": {"kernel": "tail_step_kernel", "ms": tail_ms / K, "launches_per_step": tail_n / K,
+                      "algorithmic_tflops": tfl(bf["step"], tail_ms)},
+        "tail_panel_s": {"kernel": "tail_panel_s_kernel", "ms": pans_ms / K, "launches_per_step": pans_n / K,
+                         "algorithmic_tflops": tfl(bf["panel_s"], pans_ms)},
+        "tail_panel": {"kernel": "tail_panel_kernel", "ms": panel_ms / K, "launches_per_step": panel_n / K,
+                       "algorithmic_tflops": tfl(bf["panel"], panel_ms)},
+        "perm": {"kernel": "perm_init_kernel", "ms": perm_ms / K, "launches_per_step": perm_n / K},
     }
-    tail_all = tail_ms + panel_ms
-    dominant = "tail" if tail_all >= res_ms else "residual"
-    if dominant == "tail":
-        ach = tail_fl / (tail_all / 1e3) / 1e12
-        # a double-float multiply-add takes about 12 FP32-pipe instructions (exact product of
-        # the high parts by FMA, cross terms, error-free sum), so its peak is FP32 / 12
-        peak, src = {"fp64": (NOMINAL_FP64_TFLOPS, "nominal FP64 rate (1.25 TFLOP/s)"),
-                     "fp32": (NOMINAL_FP32_TFLOPS, "nominal FP32 rate (152 SMs x 128 lanes x 2 x 2.07 GHz)"),
-                     "df64": (NOMINAL_FP32_TFLOPS / 12, "nominal FP32 rate / 12 (FP32-pipe instructions per "
-                              "double-float multiply-add)")}[args.state]
-        roof = {"kernel": f"state update ({args.state}, per-step + per-panel)", "bound": "alu", "achieved": ach,
-                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_source": src}
-    else:
+    cand = {"residual": res_ms, "tail_step": tail_ms, "tail_panel_s": pans_ms, "tail_panel": panel_ms}
+    dominant = max(cand, key=cand.get)
+    if dominant == "residual":
         ach = res_flops / (res_ms / 1e3) / 1e12
-        roof = {"kernel": f"residual ({args.chosen})", "bound": res_bound, "achieved": ach, "peak": res_peak,
+        roof = {"kernel": phases["residual"]["kernel"], "bound": res_bound, "achieved": ach, "peak": res_peak,
                 "unit": res_unit, "frac": ach / res_peak, "traffic": None,
                 "peak_source": f"{peaks['source']} bf16 sustained / {mult}" if res_bound == "tensor"
                 else "nominal FP32 rate"}
+    else:
+        fl = {"tail_step": bf["step"], "tail_panel_s": bf["panel_s"], "tail_panel": bf["panel"]}[dominant]
+        ach = fl / (cand[dominant] / 1e3) / 1e12
+        roof = {"kernel": f"{phases[dominant]['kernel']} ({args.state} state)", "bound": "alu", "achieved": ach,
+                "peak": st_peak, "unit": "TFLOP/s", "frac": ach / st_peak,
+                "traffic": measured_traffic(phases[dominant]["kernel"], args),
+                "peak_source": st_src,
+                "per_launch": "algorithmic flops of all launches / their summed CUDA-event time"}
 
-    prof_launches = int(res_n + tail_n + panel_n + perm_n) // args.steps
+    prof_launches = int(res_n + tail_n + panel_n + pans_n + perm_n) // args.steps
     out = {
         "metric": "FFS samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -577,6 +680,8 @@ def main():
     S.close()
     if not args.no_lensemble and rank == 0:
         out["lensemble"] = bench_lensemble(flags, stream)
+    if not args.no_metropolis and rank == 0:
+        out["metropolis"] = bench_metropolis(flags, stream)
     if not args.no_batching and rank == 0:
         out["batching"] = bench_batching(args, flags, stream)
     if not args.no_serving and rank == 0:

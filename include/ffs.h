@@ -231,6 +231,29 @@ int ffs_sample_lensemble(ffs_handle h, const double* lambda, int64_t B, uint64_t
                          double* out_logp, const int32_t* force_x, float* out_probs, void* cuda_stream);
 
 /*
+ * ffs_sample_metropolis - the large-L (and continuous-model) variant of Supplementary
+ * Section S-7: the column order m is drawn as usual, but x_k is drawn by a Metropolis
+ * chain of m_cond updates over sites instead of from all L conditional weights, so a
+ * step costs O(m_cond N + N k) and the sample O(m_cond N^2 + N^3), independent of L.
+ * The chain of step k starts at a uniform site and proposes uniform sites y'; a move
+ * y -> y' is accepted when u |u_y^T h|^2 < |u_{y'}^T h|^2 (the ratio of S-7; drawn sites
+ * have weight 0, so a chain that starts on one leaves it at the first proposal with
+ * weight).  Random numbers: Philox stream 3, block k (m_cond + 1) + t for iteration t
+ * (t = 0: the starting site): words 0-1 give the site floor(r L / 2^64) of their 64-bit
+ * concatenation r, words 2-3 a 53-bit uniform built like the site uniforms.  The result
+ * is exact only as m_cond grows (the chain must equilibrate; the paper leaves m_cond to
+ * the user).  A chain that ends on a site of weight 0 sets FFS_E_NUMERIC.
+ *   n_steps   fermions to place (0 = N), as ffs_sample_ex.
+ *   m_cond    Metropolis updates per step, >= 0; n_steps x (m_cond + 1) < 2^32.
+ *   out_x     device, B x n_steps int32, sites in draw order.
+ *   out_perm  device, B x N int32, or NULL: column orders m.
+ * Needs a handle with the blocked state (default flags; the residual flags are unused).
+ * Asynchronous on cuda_stream; device errors surface at ffs_sync.
+ */
+int ffs_sample_metropolis(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_index, int64_t n_steps,
+                          int64_t m_cond, int32_t* out_x, int32_t* out_perm, void* cuda_stream);
+
+/*
  * ffs_sample_batched - sample many independent instances together (the batching
  * pattern: many U of uneven L and N).  Instance i draws Bs[i] samples of handle hs[i]
  * with seed seeds[i] (sample indices 0..Bs[i]-1) into the device buffer outs[i]
@@ -318,7 +341,8 @@ int ffs_jastrow_estimate(const int32_t* x, int64_t B, int64_t n_occ, int64_t n_o
 #define FFS_PHASE_RESIDUAL 1  /* all-site weights |u_y^T h|^2 (Section S-1 products) */
 #define FFS_PHASE_TAIL 2      /* draw, pivot and per-step elimination-state update   */
 #define FFS_PHASE_PANEL 3     /* once-per-panel update of the remaining state columns */
-#define FFS_NUM_PHASES 4
+#define FFS_PHASE_PANEL_S 4   /* once-per-panel Schur complement and its inverse      */
+#define FFS_NUM_PHASES 5
 
 /*
  * ffs_profile - enable (1) or disable (0) per-phase timing of h: every kernel launch

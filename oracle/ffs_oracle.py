@@ -415,3 +415,83 @@ def lensemble_set_probabilities(C) -> dict:
         for S in itertools.combinations(range(L), n):
             out[S] = (np.linalg.det(C[np.ix_(S, S)]) if n else 1.0) / Z
     return out
+
+
+# --------------------------------------------------------------------------------------
+# Large-L / continuous-model variant (Supplementary Section S-7): x_k is drawn by a
+# Metropolis chain over sites, each move accepted with the ratio
+# |u_{y'}^T h|^2 / |u_y^T h|^2, instead of from all L conditional weights.
+# Readings (the section leaves them open): the discrete update proposes a uniform site;
+# the chain of step k starts at a uniform site; a move is accepted when
+# u * w(current) < w(proposed), which is the ratio rule for w(current) > 0 and accepts any
+# site with weight when the chain sits on a drawn site (weight 0); m_cond updates per
+# step.  Random numbers: Philox stream 3, block k (m_cond + 1) + t for iteration t
+# (t = 0 gives the starting site): words 0, 1 -> site floor(r L / 2^64) of r = w0 2^32 + w1;
+# words 2, 3 -> the 53-bit uniform, built like the site uniforms.
+STREAM_MCMC = 3
+
+
+def metropolis_randoms(seed: int, sample: int, k: int, t: int, L: int, m_cond: int):
+    """(site, uniform) of iteration t of the chain of step k."""
+    w = philox4x32_10(_ctr(k * (m_cond + 1) + t, STREAM_MCMC, sample), _key(seed))
+    r = (w[0] << 32) | w[1]
+    u = float(((w[2] >> 5) << 26) + (w[3] >> 6)) * 2.0**-53
+    return (r * L) >> 64, u
+
+
+def sample_one_metropolis(U, m_cond: int, seed: int = 0, sample: int = 0, n_steps: int | None = None,
+                          record: bool = False):
+    """One configuration with the large-L draw of Section S-7.  The column order and the
+    elimination are those of ``sample_one``; the weight of a site y at step k is
+    w(y) = |u_y^T h|^2 (0 on drawn sites), evaluated only where the chain looks.
+
+    Returns 'x' and 'm'; with record, per step 'margin': the smallest relative gap
+    |u w(current) - w(proposed)| / max(w(current), w(proposed)) over the chain's
+    decisions (how close a decision came to flipping), and 'w_final' (weight of x_k)."""
+    U = np.asarray(U)
+    L, N = U.shape
+    K = N if n_steps is None else int(n_steps)
+    dtype = np.result_type(U.dtype, np.float64)
+    m = permutation(seed, sample, N)
+    Ut = U[:, m].astype(dtype)
+    E = np.zeros((N, N), dtype)
+    x: list[int] = []
+    margins, finals = [], []
+    for k in range(K):
+        if k >= 1:       # elimination of the newest base row, as in sample_one
+            r = Ut[x[k - 1], :].copy()
+            if k >= 2:
+                c = solve_triangular(E[: k - 1, : k - 1], r[: k - 1], trans="T", lower=False)
+                r = r - c @ E[: k - 1, :]
+                r[: k - 1] = 0.0
+            E[k - 1, :] = r
+        h = np.zeros(k + 1, dtype)
+        h[k] = 1.0
+        if k:
+            h[:k] = solve_triangular(E[:k, :k], -E[:k, k], lower=False)
+        taken = set(x)
+
+        def weight(y):
+            return 0.0 if y in taken else float(abs(Ut[y, : k + 1] @ h) ** 2)
+
+        cur, _ = metropolis_randoms(seed, sample, k, 0, L, m_cond)
+        wc = weight(cur)
+        margin = math.inf
+        for t in range(1, m_cond + 1):
+            y, u = metropolis_randoms(seed, sample, k, t, L, m_cond)
+            wy = weight(y)
+            scale = max(wc, wy)
+            if scale > 0:
+                margin = min(margin, abs(u * wc - wy) / scale)
+            if u * wc < wy:
+                cur, wc = y, wy
+        if wc <= 0.0:
+            raise FloatingPointError(f"sample {sample}, step {k}: the chain found no site with weight")
+        margins.append(margin)
+        finals.append(wc)
+        x.append(int(cur))
+    out = {"x": np.array(x, dtype=np.int64), "m": m}
+    if record:
+        out["margin"] = np.array(margins)
+        out["w_final"] = np.array(finals)
+    return out

@@ -82,7 +82,6 @@ static bool blocked(const ffs_ctx* c) {
 
 static size_t state_elem_bytes(const ffs_ctx* c) { return blocked_elem_bytes(c->cplx, state_kind(c)); }
 
-// Device bytes per sample of a wave (not counting optional outputs).
 // Device bytes per sample of a wave (not counting optional outputs) for a chain of Nc
 // steps: the blocked state keeps Nc x Nc entries, the unblocked one N x N.
 static size_t state_cols(const ffs_ctx* c, int64_t Nc) { return blocked(c) ? (size_t)Nc : (size_t)c->N; }
@@ -479,8 +478,10 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
         TIMED(h, FFS_PHASE_TAIL, st, launch_blocked_step(a, bt, k, state_kind(h), op, st));
         const int64_t nb = blocked_panel_width();
         const int64_t k0 = (k / nb) * nb, k1 = (k0 + nb < n_steps) ? k0 + nb : n_steps;
-        if (k + 1 == k1 && k1 < n_steps)
-          TIMED(h, FFS_PHASE_PANEL, st, launch_blocked_panel(a, bt, k0, k1, state_kind(h), op, st));
+        if (k + 1 == k1 && k1 < n_steps) {
+          TIMED(h, FFS_PHASE_PANEL_S, st, launch_blocked_panel_s(a, bt, k0, k1, state_kind(h), st));
+          TIMED(h, FFS_PHASE_PANEL, st, launch_blocked_panel_update(a, bt, k0, k1, state_kind(h), op, st));
+        }
       } else {
         TIMED(h, FFS_PHASE_TAIL, st, launch_tail(a, k, state_fp64(h), op, st));
       }
@@ -589,6 +590,95 @@ int ffs_sample_lensemble(ffs_handle h, const double* lambda, int64_t B, uint64_t
   if (!out_n) cudaFreeAsync(nlen, st);
   cudaFreeAsync(dmax, st);
   return rc;
+}
+
+int ffs_sample_metropolis(ffs_handle h, int64_t B, uint64_t seed, uint64_t first_sample_index, int64_t n_steps,
+                          int64_t m_cond, int32_t* out_x, int32_t* out_perm, void* cuda_stream) {
+  if (!h) return fail(nullptr, FFS_E_ARG, "ffs_sample_metropolis: NULL handle");
+  if (B < 0 || m_cond < 0) return fail(h, FFS_E_ARG, "ffs_sample_metropolis: B < 0 or m_cond < 0");
+  if (n_steps == 0) n_steps = h->N;
+  if (n_steps < 1 || n_steps > h->N) return fail(h, FFS_E_ARG, "ffs_sample_metropolis: need 0 <= n_steps <= N");
+  if ((double)n_steps * (double)(m_cond + 1) > 4294967295.0)
+    return fail(h, FFS_E_ARG, "ffs_sample_metropolis: n_steps x (m_cond + 1) must stay below 2^32");
+  if (B == 0) return FFS_OK;
+  if (!out_x || !is_device_ptr(out_x) || (out_perm && !is_device_ptr(out_perm)))
+    return fail(h, FFS_E_ARG, "ffs_sample_metropolis: out_x (and out_perm) must be device memory");
+  if (!blocked(h)) return fail(h, FFS_E_UNSUPPORTED, "ffs_sample_metropolis: needs the blocked state");
+  int optin = 0;
+  FFS_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  if (mcmc_step_smem(h->N, h->cplx, state_kind(h)) > (size_t)optin - 1024)
+    return fail(h, FFS_E_UNSUPPORTED, "ffs_sample_metropolis: N too large for the shared-memory normal vectors");
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : h->stream;
+  const int state = state_kind(h);
+  const size_t es = state_elem_bytes(h), nb = blocked_panel_width(), Nc = (size_t)n_steps;
+  // per sample: m, drawn-site bits, the blocked state (no residual operand, no weights)
+  const size_t per = (size_t)h->N * 4 + (size_t)h->ldMask * 4 + (Nc * Nc + Nc * nb + nb * nb) * es;
+  size_t free_b = 0, total_b = 0;
+  FFS_CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
+  const size_t reserve = (size_t)512 << 20;
+  int64_t Bw = (int64_t)((free_b > reserve ? free_b - reserve : 0) / per);
+  if (Bw < 1) return fail(h, FFS_E_NOMEM, "ffs_sample_metropolis: not enough device memory for one sample");
+  if (Bw > B) Bw = B;
+  int32_t* m = nullptr;
+  uint32_t* mask = nullptr;
+  void *W = nullptr, *W0P = nullptr, *Sinv = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&m, (size_t)Bw * h->N * 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&mask, (size_t)Bw * h->ldMask * 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&W, (size_t)Bw * Nc * Nc * es, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&W0P, (size_t)Bw * Nc * nb * es, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&Sinv, (size_t)Bw * nb * nb * es, st);
+  for (int64_t b0 = 0; b0 < B && e == cudaSuccess; b0 += Bw) {
+    const int64_t bw = (B - b0 < Bw) ? B - b0 : Bw;
+    StepArgs a{};
+    a.L = h->L;
+    a.N = h->N;
+    a.ldMask = h->ldMask;
+    a.bw = bw;
+    a.n_steps = n_steps;
+    a.seed = seed;
+    a.first = first_sample_index + (uint64_t)b0;
+    a.cplx = h->cplx;
+    a.U64 = h->U64;
+    a.Ust = h->Ust ? h->Ust : h->U64;
+    a.m = m;
+    a.mask = mask;
+    a.x = out_x + b0 * n_steps;
+    a.ldx = n_steps;
+    a.status = h->status;
+    BlockedArgs bt{};
+    bt.Nc = n_steps;
+    bt.W = W;
+    bt.W0P = W0P;
+    bt.Sinv = Sinv;
+    e = cudaMemsetAsync(mask, 0, (size_t)bw * h->ldMask * 4, st);
+    if (e == cudaSuccess) e = launch_perm_init(a, kOpNone, st);
+    for (int64_t k = 0; k < n_steps && e == cudaSuccess; ++k) {
+      prof_begin(h, FFS_PHASE_TAIL, st);
+      e = launch_mcmc_step(a, bt, k, m_cond, state, st);
+      prof_end(h, st);
+      const int64_t k0 = (k / (int64_t)nb) * (int64_t)nb;
+      const int64_t k1 = (k0 + (int64_t)nb < n_steps) ? k0 + (int64_t)nb : n_steps;
+      if (e == cudaSuccess && k + 1 == k1 && k1 < n_steps) {
+        prof_begin(h, FFS_PHASE_PANEL_S, st);
+        e = launch_blocked_panel_s(a, bt, k0, k1, state, st);
+        prof_end(h, st);
+        if (e == cudaSuccess) {
+          prof_begin(h, FFS_PHASE_PANEL, st);
+          e = launch_blocked_panel_update(a, bt, k0, k1, state, kOpNone, st);
+          prof_end(h, st);
+        }
+      }
+    }
+    if (e == cudaSuccess && out_perm)
+      e = cudaMemcpyAsync(out_perm + b0 * h->N, m, (size_t)bw * h->N * 4, cudaMemcpyDeviceToDevice, st);
+  }
+  if (m) cudaFreeAsync(m, st);
+  if (mask) cudaFreeAsync(mask, st);
+  if (W) cudaFreeAsync(W, st);
+  if (W0P) cudaFreeAsync(W0P, st);
+  if (Sinv) cudaFreeAsync(Sinv, st);
+  if (e != cudaSuccess) return fail(h, FFS_E_CUDA, std::string("ffs_sample_metropolis: ") + cudaGetErrorString(e));
+  return FFS_OK;
 }
 
 int ffs_sample(ffs_handle h, int64_t B, uint64_t seed, int32_t* out_x) {

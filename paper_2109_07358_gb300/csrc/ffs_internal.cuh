@@ -113,7 +113,7 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-enum { kStreamPerm = 0, kStreamSite = 1, kStreamSelect = 2 };
+enum { kStreamPerm = 0, kStreamSite = 1, kStreamSelect = 2, kStreamMcmc = 3 };
 
 __host__ __device__ __forceinline__ uint4 philox_block(uint64_t seed, uint32_t block, uint32_t stream,
                                                        uint64_t sample) {

@@ -56,6 +56,17 @@ cudaError_t launch_blocked_step(const StepArgs& a, const BlockedArgs& t, int64_t
                                 cudaStream_t s);
 cudaError_t launch_blocked_panel(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int state,
                                  int op, cudaStream_t s);
+// The two halves of launch_blocked_panel (timed separately by the profiler): the panel
+// Schur complement and its inverse, then the trailing-column update.
+cudaError_t launch_blocked_panel_s(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int state,
+                                   cudaStream_t s);
+cudaError_t launch_blocked_panel_update(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int state,
+                                        int op, cudaStream_t s);
+// Large-L draw of Section S-7: a Metropolis chain of m_cond updates per step, then the
+// same per-step state update (no residual); the panel ends are launch_blocked_panel's.
+cudaError_t launch_mcmc_step(const StepArgs& a, const BlockedArgs& t, int64_t k, int64_t m_cond, int state,
+                             cudaStream_t s);
+size_t mcmc_step_smem(int64_t N, bool cplx, int state);
 size_t blocked_elem_bytes(bool cplx, int state);
 size_t blocked_step_smem(int64_t Nc, bool cplx, int state);
 int blocked_panel_width();

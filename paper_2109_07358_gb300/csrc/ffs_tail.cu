@@ -166,6 +166,10 @@ __device__ __forceinline__ int last_nonzero(const float* __restrict__ p, int64_t
   return last;
 }
 
+template <typename A>
+__device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k, int x,
+                                            int64_t len, int op_mode);
+
 // ------------------------------------------------------------------ per-step body (one warp)
 template <typename A>
 __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k,
@@ -220,6 +224,18 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
     const double iz = Z > 0.0 ? 1.0 / Z : 0.0;
     for (int64_t y = lane; y < L; y += 32) pr[y] = (float)((double)prow[y] * iz);
   }
+  step_update<A>(a, t, b, k, x, len, op_mode);
+}
+
+// ------------------------------------------------------------------ per-step state update
+// After x_k is placed: reduce its row of U against the state on the panel columns, take
+// the pivot, rank-1 update the panel columns, and write the operand of step k+1.
+template <typename A>
+__device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k, int x,
+                                            int64_t len, int op_mode) {
+  using T = Ar<A>;
+  const int lane = threadIdx.x & 31;
+  const int64_t N = a.N, Nc = t.Nc;
   if (k + 1 >= len) return;
 
   const int64_t k0 = (k / NB) * NB, i = k - k0, k1 = min(k0 + NB, Nc);
@@ -309,6 +325,76 @@ __global__ void __launch_bounds__(256) tail_step_kernel(StepArgs a, BlockedArgs 
   const int64_t b = (int64_t)blockIdx.x * kStepWarps + (threadIdx.x >> 5);
   if (b >= a.bw) return;
   step_warp<A>(a, t, b, k, op_mode);
+}
+
+// ------------------------------------------------------------------ large-L draw (Section S-7)
+// x_k from a Metropolis chain instead of the all-site weights: the chain starts at a
+// uniform site, proposes uniform sites and accepts a move y -> y' when
+// u |u_y^T h|^2 < |u_{y'}^T h|^2 (the acceptance ratio of Section S-7; a drawn site has
+// weight 0 and is never accepted).  Iteration it of step k takes Philox stream 3, block
+// k (m_cond + 1) + it: words 0-1 give the site mulhi(r, L), words 2-3 the 53-bit uniform.
+// A site's weight is its whole row of U against h scattered to the original column
+// order (-h kept in shared memory), summed by the warp and taken from lane 0, so that
+// every lane takes the same decision.
+constexpr int kMcmcWarps = 4;
+
+template <typename A>
+__device__ __forceinline__ int mcmc_draw(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k,
+                                         int64_t m_cond, A* hs) {
+  using T = Ar<A>;
+  const int lane = threadIdx.x & 31;
+  const int64_t N = a.N, Nc = t.Nc;
+  const A* W = (const A*)t.W + (size_t)b * Nc * Nc;
+  const int32_t* mrow = a.m + b * N;
+  for (int64_t c = lane; c < N; c += 32) hs[c] = T::zero();
+  __syncwarp();
+  for (int64_t j = lane; j <= k; j += 32) hs[mrow[j]] = j < k ? W[j * Nc + k] : T::neg(T::one());  // -h
+  __syncwarp();
+  const uint32_t* mk = a.mask + b * a.ldMask;
+  const A* Us = (const A*)a.Ust;
+  const uint64_t sample = a.first + (uint64_t)b;
+  auto weight = [&](int64_t y) -> double {
+    if ((mk[y >> 5] >> (y & 31)) & 1u) return 0.0;
+    const A* row = Us + y * N;
+    A acc = T::zero();
+    for (int64_t c = lane; c < N; c += 32) acc = T::fms(acc, row[c], hs[c]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc = T::add(acc, shfl_xor_any(acc, o));
+    return T::abs2(shfl_idx_any(acc, 0));
+  };
+  const uint32_t base = (uint32_t)(k * (m_cond + 1));
+  uint4 w = philox_block(a.seed, base, kStreamMcmc, sample);
+  int64_t cur = (int64_t)__umul64hi(((uint64_t)w.x << 32) | w.y, (uint64_t)a.L);
+  double pc = weight(cur);
+  for (int64_t it = 1; it <= m_cond; ++it) {
+    w = philox_block(a.seed, base + (uint32_t)it, kStreamMcmc, sample);
+    const int64_t y = (int64_t)__umul64hi(((uint64_t)w.x << 32) | w.y, (uint64_t)a.L);
+    const double u = (double)(((uint64_t)(w.z >> 5) << 26) | (uint64_t)(w.w >> 6)) * 0x1p-53;
+    const double py = weight(y);
+    if (u * pc < py) {
+      cur = y;
+      pc = py;
+    }
+  }
+  if (!(pc > 0.0) && lane == 0) set_status(a.status, FFS_E_NUMERIC);  // no site with weight reached
+  return (int)cur;
+}
+
+template <typename A>
+__global__ void __launch_bounds__(32 * kMcmcWarps) mcmc_step_kernel(StepArgs a, BlockedArgs t, int64_t k,
+                                                                   int64_t m_cond) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * kMcmcWarps + warp;
+  if (b >= a.bw) return;
+  A* hs = (A*)smem_raw + (size_t)warp * a.N;
+  const int x = mcmc_draw<A>(a, t, b, k, m_cond, hs);
+  if (lane == 0) {
+    a.x[b * a.ldx + k] = x;
+    a.mask[b * a.ldMask + (x >> 5)] |= 1u << (x & 31);
+  }
+  __syncwarp();
+  step_update<A>(a, t, b, k, x, a.n_steps, kOpNone);
 }
 
 // ------------------------------------------------------------------ panel end: S^-1
@@ -676,6 +762,22 @@ static cudaError_t group_panel_t(const GroupInst* inst, const GroupEntry* e, int
   return cudaGetLastError();
 }
 
+template <typename A>
+static cudaError_t mcmc_t(const StepArgs& a, const BlockedArgs& t, int64_t k, int64_t m_cond, cudaStream_t s) {
+  mcmc_step_kernel<A><<<(unsigned)((a.bw + kMcmcWarps - 1) / kMcmcWarps), 32 * kMcmcWarps,
+                        (size_t)kMcmcWarps * a.N * sizeof(A), s>>>(a, t, k, m_cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mcmc_step(const StepArgs& a, const BlockedArgs& t, int64_t k, int64_t m_cond, int state,
+                             cudaStream_t s) {
+  return FFS_DISPATCH_STATE(a.cplx, state, mcmc_t, a, t, k, m_cond, s);
+}
+
+size_t mcmc_step_smem(int64_t N, bool cplx, int state) {
+  return (size_t)kMcmcWarps * N * blocked_elem_bytes(cplx, state);
+}
+
 cudaError_t launch_blocked_step(const StepArgs& a, const BlockedArgs& t, int64_t k, int state, int op,
                                 cudaStream_t s) {
   return FFS_DISPATCH_STATE(a.cplx, state, step_t, a, t, k, op, s);
@@ -685,6 +787,31 @@ cudaError_t launch_blocked_panel(const StepArgs& a, const BlockedArgs& t, int64_
                                  int op, cudaStream_t s) {
   if (k1 >= t.Nc) return cudaSuccess;
   return FFS_DISPATCH_STATE(a.cplx, state, panel_t, a, t, k0, k1, op, s);
+}
+
+template <typename A>
+static cudaError_t panel_s_only_t(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, cudaStream_t s) {
+  tail_panel_s_kernel<A><<<(unsigned)a.bw, 256, panel_s_smem(sizeof(A)), s>>>(a, t, k0, k1);
+  return cudaGetLastError();
+}
+template <typename A>
+static cudaError_t panel_update_only_t(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int op,
+                                       cudaStream_t s) {
+  dim3 grid((unsigned)((t.Nc - k1 + 31) / 32), (unsigned)a.bw);
+  tail_panel_kernel<A><<<grid, 256, panel_smem(sizeof(A)), s>>>(a, t, k0, k1, op);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blocked_panel_s(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int state,
+                                   cudaStream_t s) {
+  if (k1 >= t.Nc) return cudaSuccess;
+  return FFS_DISPATCH_STATE(a.cplx, state, panel_s_only_t, a, t, k0, k1, s);
+}
+
+cudaError_t launch_blocked_panel_update(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int state,
+                                        int op, cudaStream_t s) {
+  if (k1 >= t.Nc) return cudaSuccess;
+  return FFS_DISPATCH_STATE(a.cplx, state, panel_update_only_t, a, t, k0, k1, op, s);
 }
 
 cudaError_t launch_group_step(const GroupInst* inst, const GroupEntry* e, int n, int64_t total, bool cplx,
@@ -754,6 +881,7 @@ template <typename A> static cudaError_t allow_all(int optin) {
   if (e == cudaSuccess) e = allow_smem(tail_panel_kernel<A>, optin);
   if (e == cudaSuccess) e = allow_smem(panel_s_group_kernel<A>, optin);
   if (e == cudaSuccess) e = allow_smem(panel_group_kernel<A>, optin);
+  if (e == cudaSuccess) e = allow_smem(mcmc_step_kernel<A>, optin);
   return e;
 }
 

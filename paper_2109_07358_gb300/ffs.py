@@ -82,13 +82,14 @@ def lib() -> ctypes.CDLL:
         L.ffs_server_destroy.restype = None
         L.ffs_profile.argtypes = [vp, i32]
         L.ffs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]
+        L.ffs_sample_metropolis.argtypes = [vp, i64, u64, u64, i64, i64, vp, vp, vp]
         L.ffs_sample_lensemble.argtypes = [vp, vp, i64, u64, u64, vp, vp, vp, vp, vp, vp, vp]
         L.ffs_jastrow_estimate.argtypes = [vp, i64, i64, i64, ctypes.POINTER(ffs_csr), vp, ctypes.POINTER(ffs_csr),
                                            vp, vp, vp, vp]
         for name in ("ffs_create", "ffs_create_ex", "ffs_sample", "ffs_sample_ex", "ffs_sync", "ffs_query",
                      "ffs_profile", "ffs_profile_read", "ffs_sample_noalloc", "ffs_sample_batched",
                      "ffs_server_create", "ffs_submit", "ffs_wait", "ffs_server_stats", "ffs_jastrow_estimate",
-                     "ffs_sample_lensemble"):
+                     "ffs_sample_lensemble", "ffs_sample_metropolis"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -147,6 +148,12 @@ def ffs_sample_lensemble(h, lam, B: int, seed: int, first_sample_index: int, out
     _check(lib().ffs_sample_lensemble(h, _ptr(lam), B, seed, first_sample_index, _ptr(out_x), _ptr(out_n),
                                       _ptr(out_perm), _ptr(out_logp), _ptr(force_x), _ptr(out_probs),
                                       _stream(stream)), h)
+
+
+def ffs_sample_metropolis(h, B: int, seed: int, first_sample_index: int, n_steps: int, m_cond: int, out_x,
+                          out_perm=None, stream=None):
+    _check(lib().ffs_sample_metropolis(h, B, seed, first_sample_index, n_steps, m_cond, _ptr(out_x),
+                                       _ptr(out_perm), _stream(stream)), h)
 
 
 def ffs_sample_noalloc(U, dtype: int, L: int, N: int, B: int, seed: int, out_x, stream=None):
@@ -215,9 +222,9 @@ def ffs_query(h, B: int = 0):
     return {"L": L.value, "N": N.value, "dtype": dt.value, "flags": fl.value, "bytes_for_B": bts.value}
 
 
-FFS_PHASE_PERM, FFS_PHASE_RESIDUAL, FFS_PHASE_TAIL, FFS_PHASE_PANEL = 0, 1, 2, 3
-FFS_NUM_PHASES = 4
-PHASE_NAMES = ("perm", "residual", "tail", "panel")
+FFS_PHASE_PERM, FFS_PHASE_RESIDUAL, FFS_PHASE_TAIL, FFS_PHASE_PANEL, FFS_PHASE_PANEL_S = 0, 1, 2, 3, 4
+FFS_NUM_PHASES = 5
+PHASE_NAMES = ("perm", "residual", "tail", "panel", "panel_s")
 
 
 def ffs_profile(h, enable: bool = True):
@@ -307,6 +314,21 @@ class Sampler:
             res["logp"] = lp
         if probs:
             res["probs"] = pr
+        return res
+
+    def sample_metropolis(self, B: int, m_cond: int, seed: int = 0, first_sample_index: int = 0, n_steps: int = 0,
+                          perm=False, stream=None, device="cuda"):
+        """Large-L draws (Metropolis chain of m_cond updates per step): dict with 'x'
+        (B x n_steps) and optionally 'perm'."""
+        import torch
+
+        K = n_steps or self.N
+        x = torch.empty((B, K), dtype=torch.int32, device=device)
+        pm = torch.empty((B, self.N), dtype=torch.int32, device=device) if perm else None
+        ffs_sample_metropolis(self.h, B, seed, first_sample_index, n_steps, m_cond, x, pm, stream)
+        res = {"x": x}
+        if perm:
+            res["perm"] = pm
         return res
 
     def sync(self):
