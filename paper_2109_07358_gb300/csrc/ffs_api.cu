@@ -83,8 +83,13 @@ static bool blocked(const ffs_ctx* c) {
 static size_t state_elem_bytes(const ffs_ctx* c) { return blocked_elem_bytes(c->cplx, state_kind(c)); }
 
 // Device bytes per sample of a wave (not counting optional outputs) for a chain of Nc
-// steps: the blocked state keeps Nc x Nc entries, the unblocked one N x N.
+// steps: the blocked state keeps Nc rows of round_up(Nc, 32) columns (32-column slabs),
+// the unblocked one N x N.
 static size_t state_cols(const ffs_ctx* c, int64_t Nc) { return blocked(c) ? (size_t)Nc : (size_t)c->N; }
+static size_t state_entries(const ffs_ctx* c, int64_t Nc) {
+  const size_t sc = state_cols(c, Nc);
+  return blocked(c) ? sc * ((sc + 31) / 32 * 32) : sc * sc;
+}
 static size_t per_sample_bytes_nc(const ffs_ctx* c, int64_t Nc) {
   const int op = op_mode_of(c->flags);
   const size_t sc = state_cols(c, Nc);
@@ -93,7 +98,7 @@ static size_t per_sample_bytes_nc(const ffs_ctx* c, int64_t Nc) {
   b += (size_t)c->ldMask * 4;                      // mask
   b += (size_t)c->Kp * op_elem_bytes(op);          // operand planes
   b += (size_t)c->ldP * 4;                         // weights
-  b += sc * sc * state_elem_bytes(c);              // elimination state
+  b += state_entries(c, Nc) * state_elem_bytes(c);  // elimination state
   b += 8;                                          // logp
   if (blocked(c)) {                                // panel-start columns, panel inverse
     const size_t nb = blocked_panel_width();
@@ -129,7 +134,7 @@ static void free_workspace(ffs_ctx* c) {
 // that short (marginal) chains fit more samples.
 static int ensure_workspace_nc(ffs_ctx* c, int64_t Bw, int64_t Nc) {
   const size_t sc = state_cols(c, Nc), es = state_elem_bytes(c), nb = blocked_panel_width();
-  const size_t w_need = (size_t)Bw * sc * sc * es;
+  const size_t w_need = (size_t)Bw * state_entries(c, Nc) * es;
   const size_t w0_need = blocked(c) ? (size_t)Bw * sc * nb * es : 0;
   if (Bw <= c->ws_B && w_need <= c->W_bytes && w0_need <= c->W0P_bytes) return FFS_OK;
   cudaStreamSynchronize(c->stream);
@@ -612,7 +617,8 @@ int ffs_sample_metropolis(ffs_handle h, int64_t B, uint64_t seed, uint64_t first
   const int state = state_kind(h);
   const size_t es = state_elem_bytes(h), nb = blocked_panel_width(), Nc = (size_t)n_steps;
   // per sample: m, drawn-site bits, the blocked state (no residual operand, no weights)
-  const size_t per = (size_t)h->N * 4 + (size_t)h->ldMask * 4 + (Nc * Nc + Nc * nb + nb * nb) * es;
+  const size_t Ncp = (Nc + 31) / 32 * 32;  // the state is stored in 32-column slabs
+  const size_t per = (size_t)h->N * 4 + (size_t)h->ldMask * 4 + (Nc * Ncp + Nc * nb + nb * nb) * es;
   size_t free_b = 0, total_b = 0;
   FFS_CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t reserve = (size_t)512 << 20;
@@ -624,7 +630,7 @@ int ffs_sample_metropolis(ffs_handle h, int64_t B, uint64_t seed, uint64_t first
   void *W = nullptr, *W0P = nullptr, *Sinv = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&m, (size_t)Bw * h->N * 4, st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&mask, (size_t)Bw * h->ldMask * 4, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&W, (size_t)Bw * Nc * Nc * es, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&W, (size_t)Bw * Nc * Ncp * es, st);
   if (e == cudaSuccess) e = cudaMallocAsync(&W0P, (size_t)Bw * Nc * nb * es, st);
   if (e == cudaSuccess) e = cudaMallocAsync(&Sinv, (size_t)Bw * nb * nb * es, st);
   for (int64_t b0 = 0; b0 < B && e == cudaSuccess; b0 += Bw) {

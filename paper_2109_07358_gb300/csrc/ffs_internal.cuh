@@ -172,7 +172,8 @@ struct ffs_ctx {
   uint32_t* mask = nullptr;      // Bw x ceil(L/32) chosen-site bits
   void* H = nullptr;             // Bw x Kp residual operand (per-mode element type / planes)
   float* P = nullptr;            // Bw x ldP masked weights |u_y^T h|^2 of the current step
-  void* W = nullptr;             // Bw x N x N elimination state (state precision)
+  void* W = nullptr;             // elimination state (state precision): Bw x N x N unblocked,
+                                 // Bw x Nc x round_up(Nc, 32) in 32-column slabs when blocked
   void* W0P = nullptr;           // Bw x N x 32 old rows' panel columns at the panel start
   void* Sinv = nullptr;          // Bw x 32 x 32 inverse of the panel Schur complement
   double* logp = nullptr;        // Bw

@@ -43,7 +43,8 @@ struct StepArgs {
 // Precision of the per-sample elimination state.
 enum StateKind : int { kStateFP64 = 0, kStateFP32 = 1, kStateDF64 = 2 };
 
-// Buffers of the blocked state (per sample: W N x N, W0P N x 32 panel-start copy of the
+// Buffers of the blocked state (per sample: W Nc rows x round_up(Nc, 32) columns in
+// 32-column slabs, W0P Nc x 32 panel-start copy of the
 // old rows' panel columns, Sinv 32 x 32 inverse of the panel Schur complement).
 struct BlockedArgs {
   int64_t Nc;  // state columns kept (= steps taken)

@@ -22,6 +22,12 @@
 //   the per-step updates do); tail_panel_kernel applies the two GEMM-shaped updates.
 //   In exact arithmetic this is the same state the per-step updates would produce.
 // Only the first Nc = n_steps columns are kept (marginal sampling needs no more).
+//
+// Layout of a sample's state: the columns are stored in slabs of 32; slab s holds rows
+// 0..Nc-1 of columns [32 s, 32 s + 32) contiguously, so element (j, c) sits at
+// (c / 32 * Nc + j) * 32 + c % 32 (Nc x round_up(Nc, 32) entries per sample).  The
+// columns of a panel over a range of rows, which the per-step and per-panel kernels
+// stream, are then one contiguous run of memory.
 #include <type_traits>
 
 #include "ffs_arith.cuh"
@@ -32,6 +38,9 @@
 namespace fermi {
 
 constexpr int NB = 32;           // panel width (== warp size: one lane per panel column)
+
+__device__ __forceinline__ int64_t state_stride(int64_t Nc) { return Nc * ((Nc + 31) & ~(int64_t)31); }
+__device__ __forceinline__ int64_t sidx(int64_t Nc, int64_t j, int64_t c) { return ((c >> 5) * Nc + j) * 32 + (c & 31); }
 constexpr int kStepWarps = 8;    // samples per CTA of the step kernel
 
 __device__ __forceinline__ void put_out(const StepArgs& a, int op, int64_t b, int col, double v) {
@@ -239,17 +248,18 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
   if (k + 1 >= len) return;
 
   const int64_t k0 = (k / NB) * NB, i = k - k0, k1 = min(k0 + NB, Nc);
-  const int64_t ldw = Nc;  // the state keeps Nc x Nc entries per sample
-  A* W = (A*)t.W + (size_t)b * Nc * Nc;
+  // this panel's slab: element (j, c) of the panel columns at Wp[j * 32 + c - k0]
+  A* Wp = (A*)t.W + (size_t)b * state_stride(Nc) + (size_t)(k0 >> 5) * Nc * 32;
   A* W0P = (A*)t.W0P + (size_t)b * Nc * NB;
   const int32_t* mrow = a.m + b * N;
   const A* urow = (const A*)a.Ust + (int64_t)x * N;  // U in the state type
   const int64_t c = k + lane;
   const bool cval = c < k1;
+  const int cl = (int)(c - k0);  // column within the slab
 
   // first step of a panel: keep the old rows' panel columns for the panel-end update
   if (i == 0 && k0 > 0 && lane < k1 - k0)
-    for (int64_t j = 0; j < k0; ++j) W0P[j * NB + lane] = W[j * ldw + k0 + lane];
+    for (int64_t j = 0; j < k0; ++j) W0P[j * NB + lane] = Wp[j * 32 + lane];
 
   // reduce the new row on the panel columns: r'[c] = u[c] - sum_{j<k} u[j] W[j][c]
   // (rows in groups of 8 whose loads are issued together; two accumulation chains)
@@ -262,7 +272,7 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
     for (; jj + 8 <= jn; jj += 8) {
       A wv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) wv[q] = cval ? W[(j0 + jj + q) * ldw + c] : T::zero();
+      for (int q = 0; q < 8; ++q) wv[q] = cval ? Wp[(j0 + jj + q) * 32 + cl] : T::zero();
 #pragma unroll
       for (int q = 0; q < 8; q += 2) {
         acc = T::fms(acc, shfl_idx_any(uj, jj + q), wv[q]);
@@ -271,7 +281,7 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
     }
     for (; jj < jn; ++jj) {
       const A u = shfl_idx_any(uj, jj);
-      if (cval) acc = T::fms(acc, u, W[(j0 + jj) * ldw + c]);
+      if (cval) acc = T::fms(acc, u, Wp[(j0 + jj) * 32 + cl]);
     }
   }
   acc = T::add(acc, acc2);
@@ -287,34 +297,34 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
   // rank-1 update of the panel columns (k, k1) with the old column k; then the new row
   for (int64_t j0 = 0; j0 < k; j0 += 32) {
     const int64_t jl = j0 + lane;
-    const A wj = (jl < k) ? W[jl * ldw + k] : T::zero();
+    const A wj = (jl < k) ? Wp[jl * 32 + i] : T::zero();
     const int jn = (int)min((int64_t)32, k - j0);
     int jj = 0;
     for (; jj + 8 <= jn; jj += 8) {
       A wv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) wv[q] = upd ? W[(j0 + jj + q) * ldw + c] : T::zero();
+      for (int q = 0; q < 8; ++q) wv[q] = upd ? Wp[(j0 + jj + q) * 32 + cl] : T::zero();
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const A w = shfl_idx_any(wj, jj + q);
-        if (upd) W[(j0 + jj + q) * ldw + c] = T::fms(wv[q], w, ncv);
+        if (upd) Wp[(j0 + jj + q) * 32 + cl] = T::fms(wv[q], w, ncv);
       }
     }
     for (; jj < jn; ++jj) {
       const A w = shfl_idx_any(wj, jj);
       if (upd) {
-        A* p = W + (j0 + jj) * ldw + c;
+        A* p = Wp + (j0 + jj) * 32 + cl;
         *p = T::fms(*p, w, ncv);
       }
     }
   }
-  if (upd) W[k * ldw + c] = ncv;
+  if (upd) Wp[k * 32 + cl] = ncv;
   __syncwarp();
 
   // operand of step k+1 while column k+1 is still inside this panel
   if (op_mode != kOpNone && k + 1 < k1) {
     for (int64_t j = lane; j <= k + 1; j += 32) {
-      const A v = (j <= k) ? T::neg(W[j * ldw + k + 1]) : T::one();
+      const A v = (j <= k) ? T::neg(Wp[j * 32 + i + 1]) : T::one();
       put_state<A>(a, op_mode, b, mrow[j], v);
     }
   }
@@ -344,11 +354,11 @@ __device__ __forceinline__ int mcmc_draw(const StepArgs& a, const BlockedArgs& t
   using T = Ar<A>;
   const int lane = threadIdx.x & 31;
   const int64_t N = a.N, Nc = t.Nc;
-  const A* W = (const A*)t.W + (size_t)b * Nc * Nc;
+  const A* W = (const A*)t.W + (size_t)b * state_stride(Nc);
   const int32_t* mrow = a.m + b * N;
   for (int64_t c = lane; c < N; c += 32) hs[c] = T::zero();
   __syncwarp();
-  for (int64_t j = lane; j <= k; j += 32) hs[mrow[j]] = j < k ? W[j * Nc + k] : T::neg(T::one());  // -h
+  for (int64_t j = lane; j <= k; j += 32) hs[mrow[j]] = j < k ? W[sidx(Nc, j, k)] : T::neg(T::one());  // -h
   __syncwarp();
   const uint32_t* mk = a.mask + b * a.ldMask;
   const A* Us = (const A*)a.Ust;
@@ -497,8 +507,8 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   const int64_t c0 = k1 + cb * 32;
   const int64_t c = c0 + lane;
   const bool cval = c < Nc;
-  const int64_t ldw = Nc;
-  A* W = (A*)t.W + (size_t)b * Nc * Nc;
+  // slab of the columns [c0, c0 + 32) (c0 is a multiple of 32): element (j, c0 + cc) at Wc[j * 32 + cc]
+  A* Wc = (A*)t.W + (size_t)b * state_stride(Nc) + (size_t)(c0 >> 5) * Nc * 32;
   const A* W0P = (const A*)t.W0P + (size_t)b * Nc * NB;
   const int32_t* mrow = a.m + b * N;
   const A* Us = (const A*)a.Ust;  // U in the state type
@@ -536,7 +546,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
       }
       for (int e = tid; e < 32 * 32; e += blockDim.x) {
         const int jj = e >> 5, cc = e & 31;
-        const A v = (j0 + jj < k0 && c0 + cc < Nc) ? W[(j0 + jj) * ldw + c0 + cc] : T::zero();
+        const A v = (j0 + jj < k0 && c0 + cc < Nc) ? Wc[(j0 + jj) * 32 + cc] : T::zero();
         Ws[e] = v;
         if constexpr (CX) Wsum[e] = df_add(v.re, v.im);
       }
@@ -581,7 +591,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
       }
       for (int e = tid; e < 32 * 32; e += blockDim.x) {
         const int jj = e >> 5, cc = e & 31;
-        Ws[e] = (j0 + jj < k0 && c0 + cc < Nc) ? W[(j0 + jj) * ldw + c0 + cc] : T::zero();
+        Ws[e] = (j0 + jj < k0 && c0 + cc < Nc) ? Wc[(j0 + jj) * 32 + cc] : T::zero();
       }
       __syncthreads();
 #pragma unroll 4
@@ -631,30 +641,30 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
       }
       if (cval) {
         const df p1 = lz_get(S1), p2 = lz_get(S2), p3 = lz_get(S3);
-        const A v = W[j * ldw + c];
-        W[j * ldw + c] = A{df_sub(v.re, df_sub(p1, p2)), df_sub(v.im, df_sub(df_sub(p3, p1), p2))};
+        const A v = Wc[j * 32 + lane];
+        Wc[j * 32 + lane] = A{df_sub(v.re, df_sub(p1, p2)), df_sub(v.im, df_sub(df_sub(p3, p1), p2))};
       }
       __syncwarp();
     }
     if (cval)
-      for (int jn = warp; jn < nbr; jn += 8) W[(k0 + jn) * ldw + c] = Bs[jn * 32 + lane];
+      for (int jn = warp; jn < nbr; jn += 8) Wc[(k0 + jn) * 32 + lane] = Bs[jn * 32 + lane];
   } else if (cval) {
     // old rows: Top = W0_T - W0_P Bot
     for (int64_t j = warp; j < k0; j += 8) {
-      A v = W[j * ldw + c];
+      A v = Wc[j * 32 + lane];
       const A* wp = W0P + j * NB;
       for (int ii = 0; ii < nbr; ++ii) v = T::fms(v, wp[ii], Bs[ii * 32 + lane]);
-      W[j * ldw + c] = v;
+      Wc[j * 32 + lane] = v;
     }
     // new rows: Bot
-    for (int jn = warp; jn < nbr; jn += 8) W[(k0 + jn) * ldw + c] = Bs[jn * 32 + lane];
+    for (int jn = warp; jn < nbr; jn += 8) Wc[(k0 + jn) * 32 + lane] = Bs[jn * 32 + lane];
   }
   __syncthreads();
 
   // operand of step k1 (its column is the first of T)
   if (op_mode != kOpNone && cb == 0 && k1 < a.n_steps) {
     for (int64_t j = tid; j <= k1; j += blockDim.x) {
-      const A v = (j < k1) ? T::neg(W[j * ldw + k1]) : T::one();
+      const A v = (j < k1) ? T::neg(Wc[j * 32]) : T::one();  // column k1 = c0 (cb == 0)
       put_state<A>(a, op_mode, b, mrow[j], v);
     }
   }
