@@ -238,7 +238,12 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
 
 // ------------------------------------------------------------------ per-step state update
 // After x_k is placed: reduce its row of U against the state on the panel columns, take
-// the pivot, rank-1 update the panel columns, and write the operand of step k+1.
+// the pivot, and write the operand of step k+1.  The rank-1 update of the panel columns
+// that the pivot implies is applied lazily: each step's single pass over the rows first
+// applies the previous step's update (W[j][c] -= W[j][k-1] W[k-1][c], row k-1 being that
+// step's new row), writes the row back and uses it for the reduction, so every row is
+// read and written once per step.  The arithmetic per entry is that of the eager update.
+// Lane l owns panel column k0 + l.
 template <typename A>
 __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k, int x,
                                             int64_t len, int op_mode) {
@@ -247,22 +252,24 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
   const int64_t N = a.N, Nc = t.Nc;
   if (k + 1 >= len) return;
 
-  const int64_t k0 = (k / NB) * NB, i = k - k0, k1 = min(k0 + NB, Nc);
-  // this panel's slab: element (j, c) of the panel columns at Wp[j * 32 + c - k0]
+  const int64_t k0 = (k / NB) * NB, k1 = min(k0 + NB, Nc);
+  const int i = (int)(k - k0);
+  // this panel's slab: element (j, k0 + l) at Wp[j * 32 + l]
   A* Wp = (A*)t.W + (size_t)b * state_stride(Nc) + (size_t)(k0 >> 5) * Nc * 32;
   A* W0P = (A*)t.W0P + (size_t)b * Nc * NB;
   const int32_t* mrow = a.m + b * N;
   const A* urow = (const A*)a.Ust + (int64_t)x * N;  // U in the state type
-  const int64_t c = k + lane;
-  const bool cval = c < k1;
-  const int cl = (int)(c - k0);  // column within the slab
+  const bool live = lane < k1 - k0;                  // the column exists
+  const bool need = live && lane >= i - 1;           // columns k-1 .. k1-1 are read
+  const bool gem = live && lane >= i;                // columns k .. k1-1 are reduced
+  const bool pend = i >= 1;                          // an update of step k-1 is pending
+  const bool keep = i == 0 && k0 > 0;                // first step of a panel: save W0_P
+  const A nprev = (pend && gem) ? Wp[(k - 1) * 32 + lane] : T::zero();  // new row of step k-1
+  const int src = pend ? i - 1 : 0;                  // lane of column k-1
 
-  // first step of a panel: keep the old rows' panel columns for the panel-end update
-  if (i == 0 && k0 > 0 && lane < k1 - k0)
-    for (int64_t j = 0; j < k0; ++j) W0P[j * NB + lane] = Wp[j * 32 + lane];
-
-  // reduce the new row on the panel columns: r'[c] = u[c] - sum_{j<k} u[j] W[j][c]
-  // (rows in groups of 8 whose loads are issued together; two accumulation chains)
+  // one pass over the rows: pending update, write-back, reduction
+  // r'[c] = u[c] - sum_{j<k} u[j] W[j][c] (rows in groups of 8 whose loads are issued
+  // together; two accumulation chains)
   A acc = T::zero(), acc2 = T::zero();
   for (int64_t j0 = 0; j0 < k; j0 += 32) {
     const int64_t jl = j0 + lane;
@@ -272,59 +279,66 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
     for (; jj + 8 <= jn; jj += 8) {
       A wv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) wv[q] = cval ? Wp[(j0 + jj + q) * 32 + cl] : T::zero();
+      for (int q = 0; q < 8; ++q) wv[q] = need ? Wp[(j0 + jj + q) * 32 + lane] : T::zero();
+      if (keep && live) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) W0P[(j0 + jj + q) * NB + lane] = wv[q];
+      }
+      if (pend) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const A wk = shfl_idx_any(wv[q], src);
+          if (gem && j0 + jj + q < k - 1) {
+            wv[q] = T::fms(wv[q], wk, nprev);
+            Wp[(j0 + jj + q) * 32 + lane] = wv[q];
+          }
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 8; q += 2) {
-        acc = T::fms(acc, shfl_idx_any(uj, jj + q), wv[q]);
-        acc2 = T::fms(acc2, shfl_idx_any(uj, jj + q + 1), wv[q + 1]);
+        acc = T::fms(acc, shfl_idx_any(uj, jj + q), gem ? wv[q] : T::zero());
+        acc2 = T::fms(acc2, shfl_idx_any(uj, jj + q + 1), gem ? wv[q + 1] : T::zero());
       }
     }
     for (; jj < jn; ++jj) {
+      const int64_t j = j0 + jj;
+      A w = need ? Wp[j * 32 + lane] : T::zero();
+      if (keep && live) W0P[j * NB + lane] = w;
+      if (pend) {
+        const A wk = shfl_idx_any(w, src);
+        if (gem && j < k - 1) {
+          w = T::fms(w, wk, nprev);
+          Wp[j * 32 + lane] = w;
+        }
+      }
       const A u = shfl_idx_any(uj, jj);
-      if (cval) acc = T::fms(acc, u, Wp[(j0 + jj) * 32 + cl]);
+      if (gem) acc = T::fms(acc, u, w);
     }
   }
   acc = T::add(acc, acc2);
-  const A rc = cval ? T::add(urow[mrow[c]], acc) : T::zero();
-  const A s = shfl_idx_any(rc, 0);  // pivot: the Schur residual of x_k
+  const A rc = gem ? T::add(urow[mrow[k0 + lane]], acc) : T::zero();
+  const A s = shfl_idx_any(rc, i);  // pivot: the Schur residual of x_k
   if (lane == 0) {
     const double s2 = T::abs2(s);
     if (!(s2 > 1e-300) || !isfinite(s2)) set_status(a.status, FFS_E_NUMERIC);
   }
-  const bool upd = cval && lane > 0;
+  const bool upd = gem && lane > i;
   const A ncv = upd ? T::div(rc, s) : T::zero();
-
-  // rank-1 update of the panel columns (k, k1) with the old column k; then the new row
-  for (int64_t j0 = 0; j0 < k; j0 += 32) {
-    const int64_t jl = j0 + lane;
-    const A wj = (jl < k) ? Wp[jl * 32 + i] : T::zero();
-    const int jn = (int)min((int64_t)32, k - j0);
-    int jj = 0;
-    for (; jj + 8 <= jn; jj += 8) {
-      A wv[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) wv[q] = upd ? Wp[(j0 + jj + q) * 32 + cl] : T::zero();
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const A w = shfl_idx_any(wj, jj + q);
-        if (upd) Wp[(j0 + jj + q) * 32 + cl] = T::fms(wv[q], w, ncv);
-      }
-    }
-    for (; jj < jn; ++jj) {
-      const A w = shfl_idx_any(wj, jj);
-      if (upd) {
-        A* p = Wp + (j0 + jj) * 32 + cl;
-        *p = T::fms(*p, w, ncv);
-      }
-    }
-  }
-  if (upd) Wp[k * 32 + cl] = ncv;
+  if (upd) Wp[k * 32 + lane] = ncv;  // the new row; its update of the other rows is pending
+  const A nk1 = shfl_idx_any(ncv, min(i + 1, 31));
   __syncwarp();
 
-  // operand of step k+1 while column k+1 is still inside this panel
+  // operand of step k+1 while column k+1 is still inside this panel: column k+1 after
+  // this step's (pending) update
   if (op_mode != kOpNone && k + 1 < k1) {
     for (int64_t j = lane; j <= k + 1; j += 32) {
-      const A v = (j <= k) ? T::neg(Wp[j * 32 + i + 1]) : T::one();
+      A v;
+      if (j < k)
+        v = T::neg(T::fms(Wp[j * 32 + i + 1], Wp[j * 32 + i], nk1));
+      else if (j == k)
+        v = T::neg(nk1);
+      else
+        v = T::one();
       put_state<A>(a, op_mode, b, mrow[j], v);
     }
   }
@@ -358,7 +372,18 @@ __device__ __forceinline__ int mcmc_draw(const StepArgs& a, const BlockedArgs& t
   const int32_t* mrow = a.m + b * N;
   for (int64_t c = lane; c < N; c += 32) hs[c] = T::zero();
   __syncwarp();
-  for (int64_t j = lane; j <= k; j += 32) hs[mrow[j]] = j < k ? W[sidx(Nc, j, k)] : T::neg(T::one());  // -h
+  // -h: h_j = -W[j][k] (j < k), h_k = 1, with the update of step k-1 (pending in the
+  // state, see step_update) applied to column k when k-1 is in the same panel
+  const bool pend = (k & 31) != 0;
+  const A nk = pend ? W[sidx(Nc, k - 1, k)] : T::zero();
+  for (int64_t j = lane; j <= k; j += 32) {
+    A v = T::neg(T::one());
+    if (j < k) {
+      v = W[sidx(Nc, j, k)];
+      if (pend && j < k - 1) v = T::fms(v, W[sidx(Nc, j, k - 1)], nk);
+    }
+    hs[mrow[j]] = v;
+  }
   __syncwarp();
   const uint32_t* mk = a.mask + b * a.ldMask;
   const A* Us = (const A*)a.Ust;
