@@ -42,6 +42,11 @@ constexpr int NB = 32;           // panel width (== warp size: one lane per pane
 __device__ __forceinline__ int64_t state_stride(int64_t Nc) { return Nc * ((Nc + 31) & ~(int64_t)31); }
 __device__ __forceinline__ int64_t sidx(int64_t Nc, int64_t j, int64_t c) { return ((c >> 5) * Nc + j) * 32 + (c & 31); }
 constexpr int kStepWarps = 8;    // samples per CTA of the step kernel
+// Rows of the state whose loads a step-kernel warp issues together.  Small groups keep
+// the kernel at 64 registers, so that four 256-thread CTAs fit an SM and a 4096-sample
+// step runs as one wave (measured on the 64x64 lattice workload: groups of 2 rows at 4
+// CTAs/SM 601 ms per step, groups of 8 rows at 2 CTAs/SM 670 ms).
+constexpr int kStepRowGroup = 2;
 
 __device__ __forceinline__ void put_out(const StepArgs& a, int op, int64_t b, int col, double v) {
   const size_t idx = (size_t)b * a.Kp + col;
@@ -268,25 +273,26 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
   const int src = pend ? i - 1 : 0;                  // lane of column k-1
 
   // one pass over the rows: pending update, write-back, reduction
-  // r'[c] = u[c] - sum_{j<k} u[j] W[j][c] (rows in groups of 8 whose loads are issued
+  // r'[c] = u[c] - sum_{j<k} u[j] W[j][c] (rows in groups of G whose loads are issued
   // together; two accumulation chains)
+  constexpr int G = kStepRowGroup;
   A acc = T::zero(), acc2 = T::zero();
   for (int64_t j0 = 0; j0 < k; j0 += 32) {
     const int64_t jl = j0 + lane;
     const A uj = (jl < k) ? urow[mrow[jl]] : T::zero();
     const int jn = (int)min((int64_t)32, k - j0);
     int jj = 0;
-    for (; jj + 8 <= jn; jj += 8) {
-      A wv[8];
+    for (; jj + G <= jn; jj += G) {
+      A wv[G];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) wv[q] = need ? Wp[(j0 + jj + q) * 32 + lane] : T::zero();
+      for (int q = 0; q < G; ++q) wv[q] = need ? Wp[(j0 + jj + q) * 32 + lane] : T::zero();
       if (keep && live) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) W0P[(j0 + jj + q) * NB + lane] = wv[q];
+        for (int q = 0; q < G; ++q) W0P[(j0 + jj + q) * NB + lane] = wv[q];
       }
       if (pend) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < G; ++q) {
           const A wk = shfl_idx_any(wv[q], src);
           if (gem && j0 + jj + q < k - 1) {
             wv[q] = T::fms(wv[q], wk, nprev);
@@ -295,7 +301,7 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
         }
       }
 #pragma unroll
-      for (int q = 0; q < 8; q += 2) {
+      for (int q = 0; q < G; q += 2) {
         acc = T::fms(acc, shfl_idx_any(uj, jj + q), gem ? wv[q] : T::zero());
         acc2 = T::fms(acc2, shfl_idx_any(uj, jj + q + 1), gem ? wv[q + 1] : T::zero());
       }
@@ -345,7 +351,7 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
 }
 
 template <typename A>
-__global__ void __launch_bounds__(256) tail_step_kernel(StepArgs a, BlockedArgs t, int64_t k, int op_mode) {
+__global__ void __launch_bounds__(256, 4) tail_step_kernel(StepArgs a, BlockedArgs t, int64_t k, int op_mode) {
   const int64_t b = (int64_t)blockIdx.x * kStepWarps + (threadIdx.x >> 5);
   if (b >= a.bw) return;
   step_warp<A>(a, t, b, k, op_mode);
@@ -518,12 +524,24 @@ template <typename A>
 __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t cb,
                                            int64_t k0, int64_t k1, int op_mode, unsigned char* smem_raw) {
   using T = Ar<A>;
-  A* Ys = (A*)smem_raw;     // NB x 32: Y
-  A* Bs = Ys + NB * 32;     // NB x 32: Bot
-  A* Cs = Bs + NB * 32;     // NB x 32: U[x_new, m_j] chunk
-  A* Ws = Cs + NB * 32;     // 32 x 32: W0_T chunk
-  A* Si = Ws + 32 * 32;     // NB x NB: S^-1
-  int* xs = (int*)(Si + NB * NB);
+  // Shared memory is reused between the phases (kept small so that three CTAs fit an SM):
+  //   Y phase:        Cs (NB x 32: U[x_new, m_j] chunk), Ws (32 x 32: W0_T chunk), and for
+  //                   double-float their re + im sums Csum, Wsum;
+  //   Bot/Top phases: Ys (NB x 32: Y), Si (NB x NB: S^-1), Bs (NB x 32: Bot), and for
+  //                   complex double-float Bsum and the per-warp W0_P rows Wrow, Wrs.
+  A* Cs = (A*)smem_raw;
+  A* Ws = Cs + NB * 32;
+  df* Csum = (df*)(Ws + 32 * 32);
+  df* Wsum = Csum + NB * 32;
+  A* Ys = (A*)smem_raw;
+  A* Si = Ys + NB * 32;
+  A* Bs = Si + NB * NB;
+  df* Bsum = (df*)(Bs + NB * 32);
+  A* Wrow_all = (A*)(Bsum + NB * 32);
+  df* Wrs_all = (df*)(Wrow_all + 8 * 32);
+  unsigned char* end1 = (unsigned char*)(Wsum + 32 * 32);
+  unsigned char* end2 = (unsigned char*)(Wrs_all + 8 * 32);
+  int* xs = (int*)(end1 > end2 ? end1 : end2);
   int* mj = xs + NB;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t N = a.N, Nc = t.Nc;
@@ -538,7 +556,6 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   const int32_t* mrow = a.m + b * N;
   const A* Us = (const A*)a.Ust;  // U in the state type
 
-  for (int e = tid; e < NB * NB; e += blockDim.x) Si[e] = ((const A*)t.Sinv)[(size_t)b * NB * NB + e];
   if (tid < NB) xs[tid] = tid < nbr ? a.x[b * a.ldx + k0 + tid] : 0;
   __syncthreads();
 
@@ -555,8 +572,6 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
     // (re = S1 - S2, im = S3 - S1 - S2 with S1 = sum c.re w.re, S2 = sum c.im w.im,
     // S3 = sum (c.re + c.im)(w.re + w.im)): three real products instead of four.
     constexpr bool CX = std::is_same<A, cdf>::value;
-    df* Csum = (df*)(mj + 32);  // after the index arrays (16-byte aligned)
-    df* Wsum = Csum + NB * 32;
     lzf S1[NB / 8], S2[NB / 8], S3[NB / 8];
 #pragma unroll
     for (int q = 0; q < NB / 8; ++q) S1[q] = S2[q] = S3[q] = lzf{0.f, 0.f};
@@ -628,8 +643,10 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
       __syncthreads();
     }
   }
+  __syncthreads();  // the Y-phase buffers are reused from here on
 #pragma unroll
   for (int q = 0; q < NB / 8; ++q) Ys[(warp + 8 * q) * 32 + lane] = acc[q];
+  for (int e = tid; e < NB * NB; e += blockDim.x) Si[e] = ((const A*)t.Sinv)[(size_t)b * NB * NB + e];
   __syncthreads();
 
   // Bot = S^-1 Y
@@ -644,9 +661,8 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
 
   if constexpr (std::is_same<A, cdf>::value) {
     // old rows, Karatsuba with lazy accumulators (as for Y): Top = W0_T - W0_P Bot
-    df* Bsum = (df*)(mj + 32) + NB * 32 + 32 * 32;
-    A* Wrow = (A*)(Bsum + NB * 32) + warp * 32;          // this warp's W0_P row
-    df* Wrs = (df*)((A*)(Bsum + NB * 32) + 8 * 32) + warp * 32;
+    A* Wrow = Wrow_all + warp * 32;  // this warp's W0_P row
+    df* Wrs = Wrs_all + warp * 32;
     for (int e = tid; e < NB * 32; e += blockDim.x) Bsum[e] = df_add(Bs[e].re, Bs[e].im);
     __syncthreads();
     for (int64_t j = warp; j < k0; j += 8) {
@@ -696,7 +712,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
 }
 
 template <typename A>
-__global__ void __launch_bounds__(256) tail_panel_kernel(StepArgs a, BlockedArgs t, int64_t k0, int64_t k1,
+__global__ void __launch_bounds__(256, 3) tail_panel_kernel(StepArgs a, BlockedArgs t, int64_t k0, int64_t k1,
                                                          int op_mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   panel_body<A>(a, t, blockIdx.y, blockIdx.x, k0, k1, op_mode, smem_raw);
@@ -708,13 +724,14 @@ static size_t panel_s_smem(size_t es) {
 // Ys, Bs, Cs, Ws, S^-1, the two index arrays, then (double-float) the Karatsuba sums of
 // C, W and Bot and the per-warp staged W0_P rows with their sums.
 static size_t panel_smem(size_t es) {
-  return (size_t)(NB * 32 * 3 + 32 * 32 + NB * NB) * es + 2 * 32 * 4 + (size_t)(NB * 32 * 2 + 32 * 32) * 8 +
-         (size_t)8 * 32 * (es + 8);
+  const size_t y_phase = (size_t)(NB * 32 + 32 * 32) * es + (size_t)(NB * 32 + 32 * 32) * 8;
+  const size_t bot_phase = (size_t)(NB * 32 + NB * NB + NB * 32) * es + (size_t)NB * 32 * 8 + (size_t)8 * 32 * (es + 8);
+  return (y_phase > bot_phase ? y_phase : bot_phase) + (size_t)(NB + 32) * 4;
 }
 
 // ------------------------------------------------------------------ grouped forms
 template <typename A>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     step_group_kernel(const GroupInst* __restrict__ inst, const GroupEntry* __restrict__ ent, int n, int op_mode) {
   const int64_t item = blockIdx.x;
   const int e = group_find(ent, n, item);
@@ -741,7 +758,7 @@ __global__ void __launch_bounds__(256)
 }
 
 template <typename A>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
     panel_group_kernel(const GroupInst* __restrict__ inst, const GroupEntry* __restrict__ ent, int n, int op_mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t item = blockIdx.x;
