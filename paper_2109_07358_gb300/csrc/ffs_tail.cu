@@ -444,10 +444,15 @@ template <typename A>
 __device__ __forceinline__ void panel_s_body(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k0,
                                              int64_t k1, unsigned char* smem_raw) {
   using T = Ar<A>;
-  A* Aug = (A*)smem_raw;        // NB x 2NB: [S | I] -> [I | S^-1]
-  A* Cs = Aug + NB * 2 * NB;    // NB x 32 chunk of U[x_new, m_j]
+  // the product phase's chunks and the Gauss-Jordan matrix share one region
+  A* Cs = (A*)smem_raw;         // NB x 32 chunk of U[x_new, m_j]
   A* Ws = Cs + NB * 32;         // 32 x NB chunk of W0_P
-  A* fac = Ws + 32 * NB;        // NB elimination factors, then the pivot
+  df* Csum = (df*)(Ws + 32 * NB);  // double-float: re + im of Cs and Ws (Karatsuba)
+  df* Wsum = Csum + NB * 32;
+  A* Aug = (A*)smem_raw;        // NB x 2NB: [S | I] -> [I | S^-1], after the products
+  unsigned char* end1 = (unsigned char*)(Wsum + 32 * NB);
+  unsigned char* end2 = (unsigned char*)(Aug + NB * 2 * NB);
+  A* fac = (A*)(end1 > end2 ? end1 : end2);  // NB elimination factors, then the pivot
   int* xs = (int*)(fac + NB + 1);
   int* mj = xs + NB;
   const int tid = threadIdx.x;
@@ -467,23 +472,78 @@ __device__ __forceinline__ void panel_s_body(const StepArgs& a, const BlockedArg
     const int ii = r0 + 8 * q;
     acc[q] = (ii < nbr && cc < nbr) ? Us[(int64_t)xs[ii] * N + mrow[k0 + cc]] : T::zero();
   }
-  for (int64_t j0 = 0; j0 < k0; j0 += 32) {
-    if (tid < 32) mj[tid] = (j0 + tid < k0) ? mrow[j0 + tid] : 0;
-    __syncthreads();
-    for (int e = tid; e < NB * 32; e += blockDim.x) {
-      const int ii = e >> 5, jj = e & 31;
-      Cs[e] = (ii < nbr && j0 + jj < k0) ? Us[(int64_t)xs[ii] * N + mj[jj]] : T::zero();
-      Ws[e] = (j0 + ii < k0 && jj < nbr) ? W0P[(j0 + ii) * NB + jj] : T::zero();  // row ii of the chunk
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int jj = 0; jj < 32; ++jj) {
-      const A w = Ws[jj * NB + cc];
+  if constexpr (std::is_same<A, cdf>::value || std::is_same<A, df>::value) {
+    // double-float: lazily renormalised accumulators; complex products by Karatsuba, as
+    // in the trailing update
+    constexpr bool CX = std::is_same<A, cdf>::value;
+    lzf S1[NB / 8], S2[NB / 8], S3[NB / 8];
 #pragma unroll
-      for (int q = 0; q < NB / 8; ++q) acc[q] = T::fms(acc[q], Cs[(r0 + 8 * q) * 32 + jj], w);
+    for (int q = 0; q < NB / 8; ++q) S1[q] = S2[q] = S3[q] = lzf{0.f, 0.f};
+    for (int64_t j0 = 0; j0 < k0; j0 += 32) {
+      if (tid < 32) mj[tid] = (j0 + tid < k0) ? mrow[j0 + tid] : 0;
+      __syncthreads();
+      for (int e = tid; e < NB * 32; e += blockDim.x) {
+        const int ii = e >> 5, jj = e & 31;
+        const A cv = (ii < nbr && j0 + jj < k0) ? Us[(int64_t)xs[ii] * N + mj[jj]] : T::zero();
+        const A wv = (j0 + ii < k0 && jj < nbr) ? W0P[(j0 + ii) * NB + jj] : T::zero();  // row ii of the chunk
+        Cs[e] = cv;
+        Ws[e] = wv;
+        if constexpr (CX) {
+          Csum[e] = df_add(cv.re, cv.im);
+          Wsum[e] = df_add(wv.re, wv.im);
+        }
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int jj = 0; jj < 32; ++jj) {
+        const A w = Ws[jj * NB + cc];
+        if constexpr (CX) {
+          const df wsum = Wsum[jj * NB + cc];
+#pragma unroll
+          for (int q = 0; q < NB / 8; ++q) {
+            const int ci = (r0 + 8 * q) * 32 + jj;
+            const A cv = Cs[ci];
+            lz_mac(S1[q], cv.re, w.re);
+            lz_mac(S2[q], cv.im, w.im);
+            lz_mac(S3[q], Csum[ci], wsum);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < NB / 8; ++q) lz_mac(S1[q], Cs[(r0 + 8 * q) * 32 + jj], w);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NB / 8; ++q) {
+      if constexpr (CX) {
+        const df p1 = lz_get(S1[q]), p2 = lz_get(S2[q]), p3 = lz_get(S3[q]);
+        const df re = df_sub(p1, p2), im = df_sub(df_sub(p3, p1), p2);
+        acc[q] = A{df_sub(acc[q].re, re), df_sub(acc[q].im, im)};
+      } else {
+        acc[q] = df_sub(acc[q], lz_get(S1[q]));
+      }
+    }
+  } else {
+    for (int64_t j0 = 0; j0 < k0; j0 += 32) {
+      if (tid < 32) mj[tid] = (j0 + tid < k0) ? mrow[j0 + tid] : 0;
+      __syncthreads();
+      for (int e = tid; e < NB * 32; e += blockDim.x) {
+        const int ii = e >> 5, jj = e & 31;
+        Cs[e] = (ii < nbr && j0 + jj < k0) ? Us[(int64_t)xs[ii] * N + mj[jj]] : T::zero();
+        Ws[e] = (j0 + ii < k0 && jj < nbr) ? W0P[(j0 + ii) * NB + jj] : T::zero();  // row ii of the chunk
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int jj = 0; jj < 32; ++jj) {
+        const A w = Ws[jj * NB + cc];
+#pragma unroll
+        for (int q = 0; q < NB / 8; ++q) acc[q] = T::fms(acc[q], Cs[(r0 + 8 * q) * 32 + jj], w);
+      }
+      __syncthreads();
+    }
   }
+  __syncthreads();  // the product buffers become the Gauss-Jordan matrix
 #pragma unroll
   for (int q = 0; q < NB / 8; ++q) {
     const int ii = r0 + 8 * q;
@@ -719,7 +779,9 @@ __global__ void __launch_bounds__(256, 3) tail_panel_kernel(StepArgs a, BlockedA
 }
 
 static size_t panel_s_smem(size_t es) {
-  return (size_t)(NB * 2 * NB + NB * 32 + 32 * NB + NB + 1) * es + 2 * NB * 4;
+  const size_t products = (size_t)(NB * 32 + 32 * NB) * es + (size_t)(NB * 32 + 32 * NB) * 8;
+  const size_t gj = (size_t)NB * 2 * NB * es;
+  return (products > gj ? products : gj) + (size_t)(NB + 1) * es + 2 * NB * 4;
 }
 // Ys, Bs, Cs, Ws, S^-1, the two index arrays, then (double-float) the Karatsuba sums of
 // C, W and Bot and the per-warp staged W0_P rows with their sums.
