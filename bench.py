@@ -36,6 +36,11 @@ WORKLOADS = {
         make="lattice32", B=1024, L=1024, N=256, cplx=True, grid=(32, 32),
         desc="32x32 open square lattice, random U(1) hopping phases (seed 0), N=256 lowest orbitals, "
              "complex, B=1024 samples, Philox seed 0 (reduced case for profiler captures)"),
+    "lattice32x32_N256_B4096": dict(
+        make="lattice32", B=4096, L=1024, N=256, cplx=True, grid=(32, 32),
+        desc="32x32 open square lattice, random U(1) hopping phases (seed 0), N=256 lowest orbitals, "
+             "complex, B=4096 samples, Philox seed 0 (a full 4096-sample wave at a size profilers can "
+             "replay)"),
     "chain64_N8_B10000": dict(
         make="chain", B=10000, L=64, N=8, cplx=False, grid=(1, 64),
         desc="1D open chain L=64, N=8 (closed-form orbitals), B=10^4 samples, Philox seed 0"),
@@ -114,8 +119,8 @@ def blocked_flops_per_sample(N, cplx, nb=32):
 # this workload, with the digest of the kernel sources it was taken on: once those
 # sources change the figure is stale and is reported as null.
 NCU_TRAFFIC = {
-    # 64x64 lattice, B = 4096: 31 launches of one timed step, 956.6 GB in all
-    ("tail_panel_kernel", "lattice64x64_N1024_B4096", "bf16x3", "df64"): (30.86e9, "f843aa175ac235de"),
+    # 64x64 lattice, B = 4096: 31 launches of one timed step, 1022.9 GB in all
+    ("tail_panel_kernel", "lattice64x64_N1024_B4096", "bf16x3", "df64"): (33.0e9, "602b216a99c3f570"),
 }
 KERNEL_SOURCES = ("ffs_tail.cu", "ffs_arith.cuh", "ffs_kernels.cuh", "ffs_draw.cuh", "ffs_internal.cuh")
 
