@@ -384,6 +384,38 @@ def bench_lensemble(flags, stream, B=4096, reps=3):
             "algorithmic_tflops": flops / (ms / 1e3) / 1e12}
 
 
+def bench_grouped(U, flags, B, L, N, cplx, peaks, args, stream):
+    """The opt-in grouped form on the same workload: 128 samples share a column order, so
+    step k contracts only k+1 columns (the paper's 2Lk count).  One warm-up and one timed
+    call; the residual phase's algorithmic rate against the mode's tensor peak."""
+    import torch
+
+    from paper_2109_07358_gb300 import ffs
+
+    S = ffs.Sampler(U, flags | ffs.FFS_FORM_GROUPED, stream=stream)
+    x = torch.empty((B, N), dtype=torch.int32, device="cuda")
+    ffs.ffs_sample_ex(S.h, B, 0, 0, 0, x, stream=stream)
+    S.sync()
+    ffs.ffs_profile(S.h, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ffs.ffs_sample_ex(S.h, B, 1, 0, 0, x, stream=stream)
+    e1.record(stream)
+    S.sync()
+    ms = e0.elapsed_time(e1)
+    prof = ffs.ffs_profile_read(S.h)
+    ffs.ffs_profile(S.h, False)
+    S.close()
+    res_ms = prof["residual"][0]
+    mult = {"bf16x3": 3, "fp32": 1, "tf32": 1, "bf16": 1}[args.chosen]
+    peak = peaks["bf16_sus"] / (2 if args.chosen == "tf32" else mult)
+    alg = flops_per_sample(L, N, cplx) * B / (res_ms / 1e3) / 1e12
+    return {"form": "grouped column order (128 samples per group)", "samples_per_s": B / (ms / 1e3),
+            "ms_per_step": ms, "residual_ms": res_ms, "residual_algorithmic_tflops": alg,
+            "residual_frac_of_tensor_peak": alg / peak, "tensor_peak_tflops": peak,
+            "note": "samples of a group share m (each sample is exact, the group's samples are dependent)"}
+
+
 def bench_metropolis(flags, stream, B=4096, reps=3):
     """Large-L variant (Supplementary Section S-7): open chain of L = 2^20 sites, N = 128,
     m_cond = 64 Metropolis updates per step; CUDA-event time per call of B samples,
@@ -480,6 +512,7 @@ def main():
     ap.add_argument("--no-reweight", action="store_true")
     ap.add_argument("--no-lensemble", action="store_true")
     ap.add_argument("--no-metropolis", action="store_true")
+    ap.add_argument("--no-grouped", action="store_true")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=300.0, help="serving arrivals per second")
@@ -688,6 +721,8 @@ def main():
     S.close()
     if not args.no_lensemble and rank == 0:
         out["lensemble"] = bench_lensemble(flags, stream)
+    if not args.no_grouped and rank == 0:
+        out["grouped"] = bench_grouped(U, flags, B, L, N, cplx, peaks, args, stream)
     if not args.no_metropolis and rank == 0:
         out["metropolis"] = bench_metropolis(flags, stream)
     if not args.no_batching and rank == 0:

@@ -81,6 +81,16 @@ typedef enum {
  *   FFS_FORM_BATCHED  all samples of a wave share one contraction per step (default)
  *   FFS_FORM_PLAIN    the plain per-sample form: per sample, an FP32 CUDA-core
  *                     product with the columns U[:, m_1..m_k] and an FP32 state
+ *   FFS_FORM_GROUPED  opt-in: the 128 samples of each group share one column order m, so
+ *                     that step k contracts only the k+1 leading columns of the group's
+ *                     order (K = k+1: the paper's 2Lk count instead of 2LN).  A group is
+ *                     the 128 consecutive sample indices starting at a multiple of 128;
+ *                     its m is the one the group's first index would draw alone.  Each
+ *                     sample still follows P(x) exactly, but samples of a group are
+ *                     dependent through their shared m.  Needs a tensor-core residual
+ *                     (BF16x3, BF16 or TF32) and the blocked state; first_sample_index must
+ *                     be a multiple of 128; not available to ffs_sample_batched, the serving
+ *                     engine, ffs_sample_lensemble or ffs_sample_metropolis.
  * Checks:
  *   FFS_NO_ORTHO_CHECK  skip the U^dagger U = 1 check in ffs_create_ex
  */
@@ -95,6 +105,8 @@ typedef enum {
 #define FFS_STATE_MASK 0xF0u
 #define FFS_FORM_BATCHED 0x000u
 #define FFS_FORM_PLAIN 0x100u
+#define FFS_FORM_GROUPED 0x200u
+#define FFS_GROUP_SIZE 128
 #define FFS_FORM_MASK 0xF00u
 #define FFS_NO_ORTHO_CHECK 0x1000u
 #define FFS_TAIL_UNBLOCKED 0x2000u

@@ -172,6 +172,7 @@ static void release(ffs_ctx* c) {
   cudaFree(c->UT32);
   cudaFree(c->Ust);
   cudaFree(c->sel_p);
+  cudaFree(c->Ug);
   cudaFree(c->status);
   if (c->status_host) cudaFreeHost(c->status_host);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -253,10 +254,14 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
   const bool cplx = (dtype == FFS_C128 || dtype == FFS_C64);
   if ((flags & FFS_FORM_MASK) == FFS_FORM_PLAIN)
     flags = (flags & ~(FFS_RES_MASK | FFS_STATE_MASK)) | FFS_RES_FP32 | FFS_STATE_FP32 | FFS_TAIL_UNBLOCKED;
-  if ((flags & FFS_FORM_MASK) > FFS_FORM_PLAIN || (flags & FFS_STATE_MASK) > FFS_STATE_DF64 ||
+  if ((flags & FFS_FORM_MASK) > FFS_FORM_GROUPED || (flags & FFS_STATE_MASK) > FFS_STATE_DF64 ||
       (flags & ~(FFS_RES_MASK | FFS_STATE_MASK | FFS_FORM_MASK | FFS_NO_ORTHO_CHECK | FFS_TAIL_UNBLOCKED)) ||
       op_mode_of(flags) < 0)
     return fail(nullptr, FFS_E_ARG, "ffs_create_ex: bad flags");
+  if ((flags & FFS_FORM_MASK) == FFS_FORM_GROUPED &&
+      ((flags & FFS_TAIL_UNBLOCKED) || (flags & FFS_RES_MASK) == FFS_RES_FP32))
+    return fail(nullptr, FFS_E_ARG,
+                "ffs_create_ex: the grouped form needs a tensor-core residual and the blocked state");
   if ((flags & FFS_TAIL_UNBLOCKED) && (flags & FFS_STATE_MASK) == FFS_STATE_DF64)
     return fail(nullptr, FFS_E_ARG, "ffs_create_ex: the unblocked state update has no double-float form");
 
@@ -379,11 +384,24 @@ int ffs_query(ffs_handle h, int64_t* L, int64_t* N, int* dtype, unsigned* flags,
 // each a permutation launch and then n_steps residual + state launches.  Rows of out_x,
 // force_x and out_probs are ldx steps apart.  sel_p / nlen: L-ensemble keep probabilities
 // and per-sample chain lengths (device; null for ordinary calls).
+static bool grouped_form(const ffs_ctx* c) { return (c->flags & FFS_FORM_MASK) == FFS_FORM_GROUPED; }
+
+// Bytes of one group's copy of the residual operand planes (grouped form).
+static size_t group_copy_bytes(const ffs_ctx* c) {
+  const int op = op_mode_of(c->flags);
+  const size_t planes = op == kOpBF16x3 ? 2 : 1;
+  return planes * (size_t)c->Lrp * c->Kp * (op == kOpTF32 ? 4 : 2);
+}
+
 static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_sample_index, int64_t n_steps,
                        int64_t ldx, int32_t* out_x, int32_t* out_perm, double* out_logp, const int32_t* force_x,
                        float* out_probs, cudaStream_t st, const double* sel_p, const int32_t* nlen) {
   const int op = op_mode_of(h->flags);
   const bool plain = op == kOpNone;
+  const bool grouped = grouped_form(h);
+  const int64_t G = FFS_GROUP_SIZE;
+  if (grouped && (first_sample_index % G) != 0)
+    return fail(h, FFS_E_ARG, "grouped form: first_sample_index must be a multiple of 128");
 
   const bool x_dev = is_device_ptr(out_x);
   const bool perm_dev = is_device_ptr(out_perm);
@@ -398,14 +416,31 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
   if (!x_dev) per += ldx * 4;
   if (force_x && !force_dev) per += ldx * 4;
   if (out_probs && !probs_dev) per += (size_t)ldx * h->L * 4;
+  if (grouped) per += group_copy_bytes(h) / G + 1;  // a group's operand copy, shared by its 128 samples
   size_t free_b = 0, total_b = 0;
   FFS_CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t reserve = (size_t)512 << 20;
   size_t have = free_b > reserve ? free_b - reserve : 0;
   have += (size_t)h->ws_B * per_sample_bytes_nc(h, n_steps);  // the workspace we already hold is reusable
   int64_t Bw = (int64_t)(have / per);
+  if (grouped && Bw < B) Bw = Bw / G * G;  // waves hold whole groups
   if (Bw < 1) return fail(h, FFS_E_NOMEM, "ffs_sample_ex: not enough device memory for one sample");
   if (Bw > B) Bw = B;
+  if (grouped) {
+    const int64_t groups = (Bw + G - 1) / G;
+    const size_t need = (size_t)groups * group_copy_bytes(h);
+    if (need > h->Ug_bytes) {
+      cudaStreamSynchronize(h->stream);
+      cudaStreamSynchronize(st);
+      cudaFree(h->Ug);
+      h->Ug = nullptr;
+      h->Ug_bytes = 0;
+      FFS_CUDA_TRY(h, cudaMalloc(&h->Ug, need));
+      h->Ug_bytes = need;
+      h->tmUg_key = -1;
+    }
+    h->Ug_groups = groups;
+  }
   {
     int r = ensure_workspace_nc(h, Bw, n_steps);
     if (r != FFS_OK) return r;
@@ -449,6 +484,7 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
     a.ldx = ldx;
     a.sel_p = sel_p;
     a.nlen = nlen ? nlen + b0 : nullptr;
+    a.grouped = grouped ? 1 : 0;
     if (force_x) {
       if (force_dev) {
         a.force_x = force_x + b0 * ldx;
@@ -467,6 +503,14 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
     FFS_CUDA_TRY(h, cudaMemsetAsync(h->mask, 0, (size_t)bw * h->ldMask * 4, st));
     FFS_CUDA_TRY(h, cudaMemsetAsync(h->logp, 0, (size_t)bw * 8, st));
     TIMED(h, FFS_PHASE_PERM, st, launch_perm_init(a, op, st));
+    if (grouped) {  // each group's copy of the operand planes, in the group's column order
+      const bool f32 = op == kOpTF32;
+      const void* s0 = f32 ? (const void*)h->Ue_tf32 : (const void*)h->Ue_hi;
+      const void* s1 = op == kOpBF16x3 ? (const void*)h->Ue_lo : s0;
+      TIMED(h, FFS_PHASE_PERM, st,
+            launch_group_embed(s0, s1, h->Ug, h->Lrp, h->Kp, h->Kr, h->cplx, f32, op == kOpBF16x3 ? 2 : 1, h->m, h->N,
+                               (bw + G - 1) / G, h->Ug_groups, st));
+    }
     if (!plain && op != kOpF32 && b0 == 0) {
       // column tile of the tensor-core residual: autotuned once per size class
       const int bn = residual_tile_for(h, a, op, st);
@@ -477,8 +521,10 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
         TIMED(h, FFS_PHASE_RESIDUAL, st, launch_residual_plain(a, h->UT32, k, st));
       else if (op == kOpF32)
         TIMED(h, FFS_PHASE_RESIDUAL, st, launch_residual_fp32(a, h->Ue32, st));
-      else
+      else {
+        a.kcols = grouped ? (k + 1) * (h->cplx ? 2 : 1) : 0;  // grouped: only the leading columns
         TIMED(h, FFS_PHASE_RESIDUAL, st, launch_residual_tc(h, a, op, st));
+      }
       if (blocked(h)) {
         TIMED(h, FFS_PHASE_TAIL, st, launch_blocked_step(a, bt, k, state_kind(h), op, st));
         const int64_t nb = blocked_panel_width();
@@ -541,7 +587,7 @@ int ffs_sample_lensemble(ffs_handle h, const double* lambda, int64_t B, uint64_t
   if (B < 0) return fail(h, FFS_E_ARG, "ffs_sample_lensemble: B < 0");
   if (B == 0) return FFS_OK;
   if (!lambda || !out_x) return fail(h, FFS_E_ARG, "ffs_sample_lensemble: lambda and out_x are required");
-  if (!blocked(h) || op_mode_of(h->flags) == kOpNone)
+  if (!blocked(h) || op_mode_of(h->flags) == kOpNone || grouped_form(h))
     return fail(h, FFS_E_UNSUPPORTED, "ffs_sample_lensemble: needs the batched form with the blocked state");
   for (const void* p : {(const void*)out_x, (const void*)out_n, (const void*)out_perm, (const void*)out_logp,
                         (const void*)force_x, (const void*)out_probs})
@@ -608,7 +654,8 @@ int ffs_sample_metropolis(ffs_handle h, int64_t B, uint64_t seed, uint64_t first
   if (B == 0) return FFS_OK;
   if (!out_x || !is_device_ptr(out_x) || (out_perm && !is_device_ptr(out_perm)))
     return fail(h, FFS_E_ARG, "ffs_sample_metropolis: out_x (and out_perm) must be device memory");
-  if (!blocked(h)) return fail(h, FFS_E_UNSUPPORTED, "ffs_sample_metropolis: needs the blocked state");
+  if (!blocked(h) || grouped_form(h))
+    return fail(h, FFS_E_UNSUPPORTED, "ffs_sample_metropolis: needs the blocked state and no grouped form");
   int optin = 0;
   FFS_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
   if (mcmc_step_smem(h->N, h->cplx, state_kind(h)) > (size_t)optin - 1024)

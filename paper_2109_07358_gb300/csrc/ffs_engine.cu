@@ -183,7 +183,8 @@ extern "C" int ffs_sample_batched(ffs_handle* hs, const int64_t* Bs, const uint6
   const bool cplx = c0->cplx;
   for (int i = 0; i < n; ++i) {
     ffs_ctx* c = hs[i];
-    if (!ctx_blocked(c) || ctx_op_mode(c) != op || ctx_state_kind(c) != state || c->cplx != cplx)
+    if (!ctx_blocked(c) || ctx_op_mode(c) != op || ctx_state_kind(c) != state || c->cplx != cplx ||
+        (c->flags & FFS_FORM_MASK) != FFS_FORM_BATCHED)
       return ctx_fail(c0, FFS_E_ARG,
                       "ffs_sample_batched: all handles must use the same batched tensor-core form, state "
                       "precision and real/complex type");

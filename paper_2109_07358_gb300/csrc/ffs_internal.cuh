@@ -193,6 +193,14 @@ struct ffs_ctx {
   int res_bn = 0;        // residual column tile in use (0: not chosen yet)
   int64_t tm_H_B = -1;   // workspace capacity tmH was encoded for
   double* sel_p = nullptr;       // N keep probabilities lambda / (lambda + 1) (L-ensemble calls)
+  // Grouped form: per group of 128 samples a copy of the residual operand planes with the
+  // K columns in the group's order ([planes][groups][Lrp][Kp]) and its tensor maps.
+  void* Ug = nullptr;
+  size_t Ug_bytes = 0;
+  int64_t Ug_groups = 0;
+  CUtensorMap tmUg[2];
+  int tmUg_key = -1;
+  int64_t tmUg_groups = 0;
   int* status = nullptr;         // device status word
   int* status_host = nullptr;    // pinned mirror
 

@@ -85,7 +85,9 @@ __device__ __forceinline__ bool kept_column(const StepArgs& a, uint64_t sample, 
 }
 
 __device__ __forceinline__ void perm_one(const StepArgs& a, int op_mode, int64_t b) {
-  const uint64_t sample = a.first + (uint64_t)b;
+  // grouped form: every sample of a group draws the order of the group's first index
+  const uint64_t sample = a.grouped ? (a.first + (uint64_t)b) / FFS_GROUP_SIZE * FFS_GROUP_SIZE
+                                    : a.first + (uint64_t)b;
   int32_t* m = const_cast<int32_t*>(a.m) + b * a.N;
   int64_t n = a.N;
   if (a.sel_p) {
@@ -122,11 +124,43 @@ __device__ __forceinline__ void perm_one(const StepArgs& a, int op_mode, int64_t
     ++block;
   }
   if (op_mode != kOpNone) {
+    const int col = a.grouped ? 0 : m[0];
     if (a.cplx)
-      put_operand(a, op_mode, b, m[0], cd{1.0, 0.0});
+      put_operand(a, op_mode, b, col, cd{1.0, 0.0});
     else
-      put_operand(a, op_mode, b, m[0], 1.0);
+      put_operand(a, op_mode, b, col, 1.0);
   }
+}
+
+// Grouped form: dst[g] = the operand planes with their K columns in group g's order:
+// column pair (2q, 2q + 1) of a complex embedding (column q of a real one) takes the
+// source column of U column m_g[q]; the padding columns past Kr are copied as they are.
+__global__ void group_embed_kernel(const void* src0, const void* src1, void* dst, int64_t Lrp, int64_t Kp,
+                                   int64_t Kr, bool cplx, bool f32, int planes, const int32_t* m, int64_t N,
+                                   int64_t plane_groups) {
+  const int64_t g = blockIdx.y, y = blockIdx.x;
+  const int32_t* mg = m + g * FFS_GROUP_SIZE * N;
+  for (int pl = 0; pl < planes; ++pl) {
+    const void* src = pl == 0 ? src0 : src1;
+    for (int64_t c = threadIdx.x; c < Kp; c += blockDim.x) {
+      int64_t sc = c;
+      if (c < Kr) sc = cplx ? 2 * (int64_t)mg[c >> 1] + (c & 1) : (int64_t)mg[c];
+      const size_t di = (((size_t)pl * plane_groups + g) * Lrp + y) * Kp + c;
+      if (f32)
+        ((float*)dst)[di] = ((const float*)src)[y * Kp + sc];
+      else
+        ((__nv_bfloat16*)dst)[di] = ((const __nv_bfloat16*)src)[y * Kp + sc];
+    }
+  }
+}
+
+cudaError_t launch_group_embed(const void* src0, const void* src1, void* dst, int64_t Lrp, int64_t Kp, int64_t Kr,
+                               bool cplx, bool f32, int planes, const int32_t* m, int64_t N, int64_t groups,
+                               int64_t plane_groups, cudaStream_t s) {
+  if (groups <= 0) return cudaSuccess;
+  group_embed_kernel<<<dim3((unsigned)Lrp, (unsigned)groups), 256, 0, s>>>(src0, src1, dst, Lrp, Kp, Kr, cplx, f32,
+                                                                           planes, m, N, plane_groups);
+  return cudaGetLastError();
 }
 
 // L-ensemble: the chain length of every sample (the number of kept columns) and its

@@ -38,7 +38,15 @@ struct StepArgs {
                            // samples have their own chain lengths
   const double* sel_p;     // L-ensemble: N keep probabilities of the columns, or null
   const int32_t* nlen;     // bw per-sample chain lengths (<= n_steps), or null: all n_steps
+  int grouped;             // groups of 128 samples share m; h is stored in the group's order
+  int64_t kcols;           // residual K columns in use (grouped form), 0 = all
 };
+
+// Operand column of entry j of h: the original column m_j, or position j when the group's
+// copy of the embedding is already in its column order.
+__device__ __forceinline__ int operand_col(const StepArgs& a, const int32_t* mrow, int64_t j) {
+  return a.grouped ? (int)j : mrow[j];
+}
 
 // Precision of the per-sample elimination state.
 enum StateKind : int { kStateFP64 = 0, kStateFP32 = 1, kStateDF64 = 2 };
@@ -75,6 +83,11 @@ int blocked_step_samples_per_cta();
 cudaError_t configure_blocked();
 
 cudaError_t launch_perm_init(const StepArgs& a, int op_mode, cudaStream_t s);
+// Grouped form: copies of the residual operand planes, one per group of 128 samples, with
+// the K columns in the group's order (group g's order is row 128 g of a.m).
+cudaError_t launch_group_embed(const void* src0, const void* src1, void* dst, int64_t Lrp, int64_t Kp, int64_t Kr,
+                               bool cplx, bool f32, int planes, const int32_t* m, int64_t N, int64_t groups,
+                               int64_t plane_groups, cudaStream_t s);  // planes are plane_groups copies apart
 // L-ensemble set-up: keep probabilities from the eigenvalues, then the per-sample chain
 // lengths of samples first .. first + B - 1 (a.seed, a.first, a.N, a.sel_p) and their max.
 cudaError_t launch_keep_prob(const double* lambda, int64_t N, double* p, int* status, cudaStream_t s);

@@ -106,6 +106,7 @@ __device__ __forceinline__ void residual_body(const CUtensorMap* tmA0p, const CU
       prefetch_tmap(&tmB1);
     }
     int issued = 0;
+    const int32_t jg = j0 + (b0 / 128) * p.grp_rows;  // row of Ue (or of the sample group's copy)
     for (int kb = 0; kb < nK; ++kb) {
       const int s = kb % STAGES;
       const uint32_t round = kb / STAGES;
@@ -119,8 +120,8 @@ __device__ __forceinline__ void residual_body(const CUtensorMap* tmA0p, const CU
       const int32_t x = kb * C::BK;
       tma_load_2d(st, &tmA0, full(s), x, b0);
       if (C::NA == 2) tma_load_2d(st + C::A_BYTES, &tmA1, full(s), x, b0);
-      tma_load_2d(st + C::NA * C::A_BYTES, &tmB0, full(s), x, j0);
-      if (C::NB == 2) tma_load_2d(st + C::NA * C::A_BYTES + C::B_BYTES, &tmB1, full(s), x, j0);
+      tma_load_2d(st + C::NA * C::A_BYTES, &tmB0, full(s), x, jg);
+      if (C::NB == 2) tma_load_2d(st + C::NA * C::A_BYTES + C::B_BYTES, &tmB1, full(s), x, jg);
       ++issued;
     }
     // Never leave with copies in flight: wait (bounded) for the last loads to land.
@@ -303,6 +304,21 @@ cudaError_t prepare_residual_tc_bn(ffs_ctx* c, int op, int bn) {
     }
     c->tm_U_ready = key;
   }
+  if (c->Ug && (c->tmUg_key != key || c->tmUg_groups != c->Ug_groups)) {
+    // grouped form: one map per plane over all groups' copies (groups x Lrp rows)
+    const uint64_t rows = (uint64_t)c->Ug_groups * c->Lrp;
+    const size_t es = f32 ? 4 : 2;
+    cudaError_t e = encode_2d(&c->tmUg[0], c->Ug, f32, c->Kp, rows, bn);
+    if (e != cudaSuccess) return e;
+    if (op == kOpBF16x3) {
+      e = encode_2d(&c->tmUg[1], (const char*)c->Ug + rows * c->Kp * es, false, c->Kp, rows, bn);
+      if (e != cudaSuccess) return e;
+    } else {
+      c->tmUg[1] = c->tmUg[0];
+    }
+    c->tmUg_key = key;
+    c->tmUg_groups = c->Ug_groups;
+  }
   if (c->tm_H_B != c->ws_B) {
     const uint64_t plane = (uint64_t)c->ws_B * c->Kp;
     cudaError_t e = encode_2d(&c->tmH[0], c->H, f32, c->Kp, c->ws_B, 128);
@@ -333,12 +349,15 @@ static cudaError_t launch_cfg(ffs_ctx* c, const StepArgs& a, cudaStream_t s) {
   p.ldP = a.ldP;
   p.ldMask = a.ldMask;
   p.nK = (int)(a.Kp / Cf::BK);
+  if (a.grouped && a.kcols > 0) p.nK = (int)((a.kcols + Cf::BK - 1) / Cf::BK);  // the leading K columns
   p.cplx = a.cplx ? 1 : 0;
+  p.grp_rows = a.grouped ? (int)c->Lrp : 0;
   p.P = a.P;
   p.mask = a.mask;
   p.status = a.status;
   dim3 grid((unsigned)(c->Lrp / BN), (unsigned)((a.bw + 127) / 128));
-  residual_tc_kernel<BN, STAGES, KIND><<<grid, 192, Cf::SMEM, s>>>(c->tmH[0], c->tmH[1], c->tmU[0], c->tmU[1], p);
+  const CUtensorMap* tu = a.grouped ? c->tmUg : c->tmU;
+  residual_tc_kernel<BN, STAGES, KIND><<<grid, 192, Cf::SMEM, s>>>(c->tmH[0], c->tmH[1], tu[0], tu[1], p);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@ struct TcArgs {
   int64_t bw, L, ldP, ldMask;
   int nK;
   int cplx;
+  int grp_rows;  // grouped form: rows of one group's copy of Ue (row offset of sample tile t: t x grp_rows)
   float* P;
   const uint32_t* mask;
   int* status;

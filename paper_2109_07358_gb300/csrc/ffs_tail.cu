@@ -345,7 +345,7 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
         v = T::neg(nk1);
       else
         v = T::one();
-      put_state<A>(a, op_mode, b, mrow[j], v);
+      put_state<A>(a, op_mode, b, operand_col(a, mrow, j), v);
     }
   }
 }
@@ -766,7 +766,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   if (op_mode != kOpNone && cb == 0 && k1 < a.n_steps) {
     for (int64_t j = tid; j <= k1; j += blockDim.x) {
       const A v = (j < k1) ? T::neg(Wc[j * 32]) : T::one();  // column k1 = c0 (cb == 0)
-      put_state<A>(a, op_mode, b, mrow[j], v);
+      put_state<A>(a, op_mode, b, operand_col(a, mrow, j), v);
     }
   }
 }

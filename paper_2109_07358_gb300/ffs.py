@@ -33,6 +33,8 @@ FFS_STATE_FP32 = 0x10
 FFS_STATE_DF64 = 0x20
 FFS_FORM_BATCHED = 0x000
 FFS_FORM_PLAIN = 0x100
+FFS_FORM_GROUPED = 0x200
+FFS_GROUP_SIZE = 128
 FFS_NO_ORTHO_CHECK = 0x1000
 FFS_TAIL_UNBLOCKED = 0x2000
 
