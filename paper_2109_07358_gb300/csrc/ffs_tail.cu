@@ -749,6 +749,19 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
     }
     if (cval)
       for (int jn = warp; jn < nbr; jn += 8) Wc[(k0 + jn) * 32 + lane] = Bs[jn * 32 + lane];
+  } else if constexpr (std::is_same<A, df>::value) {
+    // old rows with a lazy accumulator, the warp's W0_P row staged in shared memory
+    A* Wrow = Wrow_all + warp * 32;
+    for (int64_t j = warp; j < k0; j += 8) {
+      if (lane < nbr) Wrow[lane] = W0P[j * NB + lane];
+      __syncwarp();
+      lzf S1{0.f, 0.f};
+      for (int ii = 0; ii < nbr; ++ii) lz_mac(S1, Wrow[ii], Bs[ii * 32 + lane]);
+      if (cval) Wc[j * 32 + lane] = df_sub(Wc[j * 32 + lane], lz_get(S1));
+      __syncwarp();
+    }
+    if (cval)
+      for (int jn = warp; jn < nbr; jn += 8) Wc[(k0 + jn) * 32 + lane] = Bs[jn * 32 + lane];
   } else if (cval) {
     // old rows: Top = W0_T - W0_P Bot
     for (int64_t j = warp; j < k0; j += 8) {
