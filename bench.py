@@ -104,9 +104,10 @@ def blocked_flops_per_sample(N, cplx, nb=32):
       panel_s  per panel with trailing columns: S = D - C W0_P (nb x k0 x nb) and its
                Gauss-Jordan inverse (nb x nb x 2 nb);
       panel    per panel, T = [k1, N): Y = U - C W0_T (nb x k0 x |T|), S^-1 Y
-               (nb x nb x |T|), W0_T - W0_P Bot (k0 x nb x |T|)."""
+               (nb x nb x |T|), W0_T - W0_P Bot (k0 x nb x |T|);
+      top      the last of these alone (the part the tensor-core trailing update takes)."""
     f = 8 if cplx else 2
-    step = panel_s = panel = 0.0
+    step = panel_s = panel = top = 0.0
     for k in range(N - 1):
         k0 = (k // nb) * nb
         k1 = min(k0 + nb, N)
@@ -118,7 +119,8 @@ def blocked_flops_per_sample(N, cplx, nb=32):
         T = N - k1
         panel_s += nb * k0 * nb + nb * nb * 2 * nb
         panel += T * nb * (2 * k0 + nb)
-    return {"step": step * f, "panel_s": panel_s * f, "panel": panel * f}
+        top += T * nb * k0
+    return {"step": step * f, "panel_s": panel_s * f, "panel": panel * f, "top": top * f}
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
@@ -508,6 +510,9 @@ def main():
     ap.add_argument("--B", type=int, default=0, help="override samples per step")
     ap.add_argument("--chosen", default="bf16x3", choices=["bf16x3", "fp32", "tf32", "bf16"])
     ap.add_argument("--state", default="df64", choices=["df64", "fp64", "fp32"])
+    ap.add_argument("--no-trailing-tc", dest="trailing_tc", action="store_false",
+                    help="keep the old rows' trailing update on the CUDA cores (default: tensor cores, BF16 "
+                         "slices of the double-float operands)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -561,7 +566,8 @@ def main():
     res_flag = {"bf16x3": ffs.FFS_RES_BF16X3, "fp32": ffs.FFS_RES_FP32, "tf32": ffs.FFS_RES_TF32,
                 "bf16": ffs.FFS_RES_BF16}[args.chosen]
     state_flag = {"df64": ffs.FFS_STATE_DF64, "fp64": ffs.FFS_STATE_FP64, "fp32": ffs.FFS_STATE_FP32}[args.state]
-    flags = res_flag | state_flag
+    flags = res_flag | state_flag | (ffs.FFS_TRAILING_TC if args.trailing_tc and cplx else 0)
+    flags_real = flags & ~ffs.FFS_TRAILING_TC  # the sections with real or mixed U
     stream = torch.cuda.Stream()
     S = ffs.Sampler(U, flags, stream=stream)
     x = torch.empty((B, N), dtype=torch.int32, device="cuda")
@@ -602,6 +608,7 @@ def main():
     tail_ms, tail_n = prof["tail"]
     panel_ms, panel_n = prof["panel"]
     pans_ms, pans_n = prof["panel_s"]
+    ptc_ms, ptc_n = prof["panel_tc"]
     perm_ms, perm_n = prof["perm"]
     K = args.steps
     res_flops = flops_per_sample(L, N, cplx) * B * K
@@ -633,9 +640,12 @@ def main():
         "tail_panel_s": {"kernel": "tail_panel_s_kernel", "ms": pans_ms / K, "launches_per_step": pans_n / K,
                          "algorithmic_tflops": tfl(bf["panel_s"], pans_ms)},
         "tail_panel": {"kernel": "tail_panel_kernel", "ms": panel_ms / K, "launches_per_step": panel_n / K,
-                       "algorithmic_tflops": tfl(bf["panel"], panel_ms)},
+                       "algorithmic_tflops": tfl(bf["panel"] - (bf["top"] if ptc_n else 0.0), panel_ms)},
         "perm": {"kernel": "perm_init_kernel", "ms": perm_ms / K, "launches_per_step": perm_n / K},
     }
+    if ptc_n:
+        phases["tail_panel_tc"] = {"kernel": "oz_top_kernel (+ slices, operand)", "ms": ptc_ms / K,
+                                   "launches_per_step": ptc_n / K, "algorithmic_tflops": tfl(bf["top"], ptc_ms)}
     cand = {"residual": res_ms, "tail_step": tail_ms, "tail_panel_s": pans_ms, "tail_panel": panel_ms}
     dominant = max(cand, key=cand.get)
     if dominant == "residual":
@@ -645,7 +655,8 @@ def main():
                 "peak_source": f"{peaks['source']} bf16 sustained / {mult}" if res_bound == "tensor"
                 else "nominal FP32 rate"}
     else:
-        fl = {"tail_step": bf["step"], "tail_panel_s": bf["panel_s"], "tail_panel": bf["panel"]}[dominant]
+        fl = {"tail_step": bf["step"], "tail_panel_s": bf["panel_s"],
+              "tail_panel": bf["panel"] - (bf["top"] if ptc_n else 0.0)}[dominant]
         ach = fl / (cand[dominant] / 1e3) / 1e12
         roof = {"kernel": f"{phases[dominant]['kernel']} ({args.state} state)", "bound": "alu", "achieved": ach,
                 "peak": st_peak, "unit": "TFLOP/s", "frac": ach / st_peak,
@@ -653,14 +664,16 @@ def main():
                 "peak_source": st_src,
                 "per_launch": "algorithmic flops of all launches / their summed CUDA-event time"}
 
-    prof_launches = int(res_n + tail_n + panel_n + pans_n + perm_n) // args.steps
+    prof_launches = int(res_n + tail_n + panel_n + pans_n + ptc_n + perm_n) // args.steps
     out = {
         "metric": "FFS samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64" if cplx else "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": spec["desc"], "L": L, "N": N, "B": B,
-                   "form": f"batched {args.chosen} residual + {args.state} state", "l2": "inputs larger than L2 "
+                   "form": f"batched {args.chosen} residual + {args.state} state" +
+                           (" + tensor-core trailing update" if flags & ffs.FFS_TRAILING_TC else ""),
+                   "l2": "inputs larger than L2 "
                    "(the per-sample state of a batch is tens of GB)"},
         "clocks": clk.summary(),
         "gpu_launches": prof_launches,
@@ -728,15 +741,15 @@ def main():
                       "d2h_bytes_per_step": int(x_host.numel() * 4)}
 
     if not args.no_lensemble and rank == 0:
-        out["lensemble"] = bench_lensemble(flags, stream)
+        out["lensemble"] = bench_lensemble(flags_real, stream)
     if not args.no_grouped and rank == 0:
         out["grouped"] = bench_grouped(U, flags, B, L, N, cplx, peaks, args, stream)
     if not args.no_metropolis and rank == 0:
-        out["metropolis"] = bench_metropolis(flags, stream)
+        out["metropolis"] = bench_metropolis(flags_real, stream)
     if not args.no_batching and rank == 0:
         out["batching"] = bench_batching(args, flags, stream)
     if not args.no_serving and rank == 0:
-        out["serving"] = bench_serving(args, flags)
+        out["serving"] = bench_serving(args, flags_real)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -91,6 +91,12 @@ typedef enum {
  *                     (BF16x3, BF16 or TF32) and the blocked state; first_sample_index must
  *                     be a multiple of 128; not available to ffs_sample_batched, the serving
  *                     engine, ffs_sample_lensemble or ffs_sample_metropolis.
+ * Trailing update:
+ *   FFS_TRAILING_TC  opt-in: the once-per-panel update of the old rows' remaining columns
+ *                    runs on the tensor cores through an error-free split of the
+ *                    double-float operands into BF16 slices (products exact in FP32
+ *                    accumulation, double-float epilogue).  Complex U, FFS_STATE_DF64 and
+ *                    the blocked state only (else FFS_E_UNSUPPORTED at creation).
  * Checks:
  *   FFS_NO_ORTHO_CHECK  skip the U^dagger U = 1 check in ffs_create_ex
  */
@@ -110,6 +116,7 @@ typedef enum {
 #define FFS_FORM_MASK 0xF00u
 #define FFS_NO_ORTHO_CHECK 0x1000u
 #define FFS_TAIL_UNBLOCKED 0x2000u
+#define FFS_TRAILING_TC 0x4000u
 
 /* Tolerance of the orthonormality check: max_ij |(U^dagger U)_ij - delta_ij|. */
 #define FFS_ORTHO_TOL 1e-6
@@ -354,7 +361,8 @@ int ffs_jastrow_estimate(const int32_t* x, int64_t B, int64_t n_occ, int64_t n_o
 #define FFS_PHASE_TAIL 2      /* draw, pivot and per-step elimination-state update   */
 #define FFS_PHASE_PANEL 3     /* once-per-panel update of the remaining state columns */
 #define FFS_PHASE_PANEL_S 4   /* once-per-panel Schur complement and its inverse      */
-#define FFS_NUM_PHASES 5
+#define FFS_PHASE_PANEL_TC 5  /* FFS_TRAILING_TC: slices and tensor-core old-row update */
+#define FFS_NUM_PHASES 6
 
 /*
  * ffs_profile - enable (1) or disable (0) per-phase timing of h: every kernel launch

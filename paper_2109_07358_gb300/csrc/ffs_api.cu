@@ -173,6 +173,7 @@ static void release(ffs_ctx* c) {
   cudaFree(c->Ust);
   cudaFree(c->sel_p);
   cudaFree(c->Ug);
+  cudaFree(c->oz_buf);
   cudaFree(c->status);
   if (c->status_host) cudaFreeHost(c->status_host);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -252,10 +253,17 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
   if (ldU < N) return fail(nullptr, FFS_E_ARG, "ffs_create_ex: need ldU >= N");
   if (L > (int64_t)1 << 30) return fail(nullptr, FFS_E_ARG, "ffs_create_ex: L too large");
   const bool cplx = (dtype == FFS_C128 || dtype == FFS_C64);
+  if ((flags & FFS_TRAILING_TC) &&
+      (!cplx || (flags & FFS_STATE_MASK) != FFS_STATE_DF64 || (flags & FFS_TAIL_UNBLOCKED) ||
+       (flags & FFS_FORM_MASK) == FFS_FORM_PLAIN || (flags & FFS_RES_MASK) == FFS_RES_FP32))
+    return fail(nullptr, FFS_E_UNSUPPORTED,
+                "ffs_create_ex: the tensor-core trailing update needs complex U, the double-float state, the "
+                "blocked state and a tensor-core residual");
   if ((flags & FFS_FORM_MASK) == FFS_FORM_PLAIN)
     flags = (flags & ~(FFS_RES_MASK | FFS_STATE_MASK)) | FFS_RES_FP32 | FFS_STATE_FP32 | FFS_TAIL_UNBLOCKED;
   if ((flags & FFS_FORM_MASK) > FFS_FORM_GROUPED || (flags & FFS_STATE_MASK) > FFS_STATE_DF64 ||
-      (flags & ~(FFS_RES_MASK | FFS_STATE_MASK | FFS_FORM_MASK | FFS_NO_ORTHO_CHECK | FFS_TAIL_UNBLOCKED)) ||
+      (flags & ~(FFS_RES_MASK | FFS_STATE_MASK | FFS_FORM_MASK | FFS_NO_ORTHO_CHECK | FFS_TAIL_UNBLOCKED |
+                 FFS_TRAILING_TC)) ||
       op_mode_of(flags) < 0)
     return fail(nullptr, FFS_E_ARG, "ffs_create_ex: bad flags");
   if ((flags & FFS_FORM_MASK) == FFS_FORM_GROUPED &&
@@ -300,6 +308,7 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
       CREATE_TRY(configure_kernels(N, cplx));
       CREATE_TRY(configure_residual_tc());
       CREATE_TRY(configure_blocked());
+      CREATE_TRY(configure_oz());
       configured[c->device] = true;
     }
   }
@@ -399,6 +408,7 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
   const int op = op_mode_of(h->flags);
   const bool plain = op == kOpNone;
   const bool grouped = grouped_form(h);
+  const bool tc_top = (h->flags & FFS_TRAILING_TC) && blocked(h);
   const int64_t G = FFS_GROUP_SIZE;
   if (grouped && (first_sample_index % G) != 0)
     return fail(h, FFS_E_ARG, "grouped form: first_sample_index must be a multiple of 128");
@@ -417,6 +427,7 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
   if (force_x && !force_dev) per += ldx * 4;
   if (out_probs && !probs_dev) per += (size_t)ldx * h->L * 4;
   if (grouped) per += group_copy_bytes(h) / G + 1;  // a group's operand copy, shared by its 128 samples
+  if (tc_top) per += oz_bytes_per_sample(n_steps);   // slices of the tensor-core trailing update
   size_t free_b = 0, total_b = 0;
   FFS_CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t reserve = (size_t)512 << 20;
@@ -445,6 +456,7 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
     int r = ensure_workspace_nc(h, Bw, n_steps);
     if (r != FFS_OK) return r;
   }
+  if (tc_top) FFS_CUDA_TRY(h, oz_prepare(h, Bw, n_steps));
   int32_t* xbuf = nullptr;
   int32_t* fbuf = nullptr;
   float* pbuf = nullptr;
@@ -531,7 +543,10 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
         const int64_t k0 = (k / nb) * nb, k1 = (k0 + nb < n_steps) ? k0 + nb : n_steps;
         if (k + 1 == k1 && k1 < n_steps) {
           TIMED(h, FFS_PHASE_PANEL_S, st, launch_blocked_panel_s(a, bt, k0, k1, state_kind(h), st));
+          bt.tc_top = tc_top ? 1 : 0;  // then the old rows and the next operand are the tensor-core pass's
           TIMED(h, FFS_PHASE_PANEL, st, launch_blocked_panel_update(a, bt, k0, k1, state_kind(h), op, st));
+          if (tc_top) TIMED(h, FFS_PHASE_PANEL_TC, st, launch_oz_top(h, a, bt, k0, k1, op, st));
+          bt.tc_top = 0;
         }
       } else {
         TIMED(h, FFS_PHASE_TAIL, st, launch_tail(a, k, state_fp64(h), op, st));

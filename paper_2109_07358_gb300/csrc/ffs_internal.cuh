@@ -136,6 +136,16 @@ __host__ __device__ __forceinline__ double select_uniform(uint64_t seed, uint64_
   return (double)bits * 0x1p-53;
 }
 
+// Slice buffers of the tensor-core trailing update: A [b][slice][KP][64] and B
+// [b][slice][re/im][TP][64] BF16, row scales As [b][KP] and column scales Bs [b][TP].
+struct OzArgs {
+  __nv_bfloat16* A;
+  __nv_bfloat16* B;
+  float* As;
+  float* Bs;
+  int64_t KP, TP;
+};
+
 // ------------------------------------------------------------------ status word
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
@@ -193,6 +203,13 @@ struct ffs_ctx {
   int res_bn = 0;        // residual column tile in use (0: not chosen yet)
   int64_t tm_H_B = -1;   // workspace capacity tmH was encoded for
   double* sel_p = nullptr;       // N keep probabilities lambda / (lambda + 1) (L-ensemble calls)
+  // Tensor-core trailing update (FFS_TRAILING_TC): BF16 slices of W0_P and Bot, their
+  // power-of-two scales, and the tensor maps of the slice planes.
+  void* oz_buf = nullptr;
+  size_t oz_bytes = 0;
+  fermi::OzArgs oz{};
+  CUtensorMap ozA, ozB;
+  int64_t oz_key_B = -1, oz_key_Nc = -1;
   // Grouped form: per group of 128 samples a copy of the residual operand planes with the
   // K columns in the group's order ([planes][groups][Lrp][Kp]) and its tensor maps.
   void* Ug = nullptr;

@@ -59,6 +59,7 @@ struct BlockedArgs {
   void* W;
   void* W0P;
   void* Sinv;
+  int tc_top;  // the old rows' trailing update (Top) and the next operand are done elsewhere
 };
 
 cudaError_t launch_blocked_step(const StepArgs& a, const BlockedArgs& t, int64_t k, int state, int op,
@@ -71,6 +72,16 @@ cudaError_t launch_blocked_panel_s(const StepArgs& a, const BlockedArgs& t, int6
                                    cudaStream_t s);
 cudaError_t launch_blocked_panel_update(const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int state,
                                         int op, cudaStream_t s);
+// Operand of step k1 from column k1 of the state (after every row of it is updated).
+cudaError_t launch_column_operand(const StepArgs& a, const BlockedArgs& t, int64_t k1, int state, int op,
+                                  cudaStream_t s);
+// Tensor-core Top update (ffs_ozaki.cu): slices of W0_P and Bot, the product, the operand.
+cudaError_t launch_oz_top(ffs_ctx* c, const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int op,
+                          cudaStream_t s);
+cudaError_t oz_prepare(ffs_ctx* c, int64_t Bw, int64_t Nc);
+size_t oz_bytes_per_sample(int64_t Nc);
+cudaError_t configure_oz();
+
 // Large-L draw of Section S-7: a Metropolis chain of m_cond updates per step, then the
 // same per-step state update (no residual); the panel ends are launch_blocked_panel's.
 cudaError_t launch_mcmc_step(const StepArgs& a, const BlockedArgs& t, int64_t k, int64_t m_cond, int state,

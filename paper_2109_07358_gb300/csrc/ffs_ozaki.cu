@@ -1,0 +1,397 @@
+// Trailing update of the old rows on tensor cores (opt-in, complex double-float state).
+//
+// At a panel end the old rows' trailing columns take Top = W0_T - W0_P Bot (the
+// block-inverse identity of the blocked state, see ffs_tail.cu): per sample a
+// (k0 x 32) by (32 x |T|) complex product in double-float precision.  Here the product
+// runs on tcgen05 tensor cores through an error-free split of the operands into BF16
+// slices (Ozaki, Ogita, Oishi & Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its applications",
+// Numer. Algorithms 59, 2012):
+//   * each row r of A = [Re W0_P | Im W0_P] (64 reals) is scaled by a power of two
+//     sigma_r >= its largest entry and cut into six 8-bit integer slices,
+//     A_r / sigma_r = sum_i a_i 2^(-7 - 8(i-1)), |a_i| <= 128 (exact in BF16);
+//   * each trailing column c of B, [Re Bot ; -Im Bot] for the real part of the product
+//     and [Im Bot ; Re Bot] for the imaginary part, likewise with sigma_c;
+//   * the slice products a_i b_j with i + j = d <= 8 accumulate in one FP32 tensor-memory
+//     accumulator per d: every partial sum is an integer below 2^23, so the tensor-core
+//     accumulation is exact;
+//   * the epilogue adds the seven accumulators in double-float, scales by
+//     sigma_r sigma_c 2^(-14 - 8(d-2)) and subtracts from W0_T.
+// The dropped slice products (i + j > 8) are below 2^-46 of sigma_r sigma_c K, the order
+// of the double-float rounding of the direct update.
+//
+// Kernels per panel end: slices of A (one warp per row), slices of B (one warp per
+// column), the product (one CTA per sample and 128 old rows, looping over the trailing
+// 32-column slabs; warp 0 issues TMA, warp 1 the MMAs, warps 2-17 the epilogue, four
+// per 32-lane quarter of tensor memory, each for 8 of the 32 columns), and the operand of
+// the next step from the updated column.
+#include <cfloat>
+
+#include "ffs_arith.cuh"
+#include "ffs_kernels.cuh"
+#include "ffs_residual_tc.cuh"
+#include "ffs_sm100.cuh"
+
+namespace fermi {
+
+using namespace sm100;
+
+namespace {
+
+constexpr int kSlices = 6;      // 8-bit slices per operand (48 bits)
+constexpr int kDmax = 8;        // slice products a_i b_j kept: i + j <= kDmax
+constexpr int kNumD = kDmax - 1;  // accumulator groups d = 2 .. kDmax
+constexpr int MT = 128;         // old rows per CTA
+constexpr int NT = 32;          // trailing columns per tile (one slab)
+constexpr uint32_t kARows = MT, kBRows = NT;
+constexpr uint32_t kATile = kARows * 128;     // one slice tile: 128 rows x 64 BF16
+constexpr uint32_t kBTile = kBRows * 128;     // one slice tile: 32 rows x 64 BF16
+constexpr uint32_t kABytes = kSlices * kATile;                 // 96 KB
+constexpr uint32_t kBStage = kSlices * 2 * kBTile;             // 48 KB (six slices, re and im columns)
+constexpr int kBStages = 1;
+// Epilogue staging of the product, one 32-row block per TMEM lane quarter, rows padded
+// by 16 bytes against bank conflicts: the quarter's warps then update its rows of W0_T
+// with lanes over columns (coalesced 512-byte rows; measured faster than each thread
+// updating its own row directly, which leaves two B stages room in shared memory).
+constexpr uint32_t kPRow = NT * 16 + 16;
+constexpr int kEpiWarps = 16;
+constexpr int kEpiCols = NT / (kEpiWarps / 4);  // columns (and staged rows) per epilogue warp
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr uint32_t kPStage = 4 * 32 * kPRow;
+constexpr uint32_t kSmem = kABytes + kBStages * kBStage + kPStage + 1024 + 256;
+constexpr uint32_t kTmemCols = 512;             // 2 x 7 accumulators of 32 columns = 448
+constexpr uint32_t kIdesc = idesc_bf16(MT, NT);
+
+// The six slices of x (|x| < 1): x 2^7 = a_1 + 2^-8 (a_2 + 2^-8 (a_3 + ...)), each a_i an
+// integer in [-128, 128].  Every step is exact in double-float arithmetic.
+__device__ __forceinline__ void df_slices(df x, float (&s)[kSlices]) {
+  float th = x.hi * 128.f, tl = x.lo * 128.f;
+#pragma unroll
+  for (int i = 0; i < kSlices; ++i) {
+    const float a = rintf(th);
+    const df r = two_sum(th - a, tl);  // th - a is exact (|th| <= 2^7 + 1)
+    s[i] = a;
+    th = r.hi * 256.f;
+    tl = r.lo * 256.f;
+  }
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Power-of-two scale sigma >= max, as (sigma, 1/sigma); 1 for an all-zero vector.
+__device__ __forceinline__ void pow2_scale(float mx, float& sigma, float& inv) {
+  if (!(mx > 0.f)) {
+    sigma = inv = 1.f;
+    return;
+  }
+  int e;
+  frexpf(mx, &e);  // mx = m 2^e, m in [0.5, 1): mx < 2^e
+  sigma = ldexpf(1.f, e);
+  inv = ldexpf(1.f, -e);
+}
+
+__device__ __forceinline__ df df_scale(df v, float p2) { return {v.hi * p2, v.lo * p2}; }  // exact (power of 2)
+
+// A slices: rows r < k0 of W0_P.  Layout [b][slice][KP][64] BF16, sigma_r in As[b][KP].
+__global__ void __launch_bounds__(256) oz_slice_a_kernel(StepArgs a, BlockedArgs t, OzArgs z, int64_t k0,
+                                                          int64_t k1) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = blockIdx.y;
+  const int64_t r = (int64_t)blockIdx.x * 8 + warp;
+  if (r >= k0) return;
+  if (a.nlen && a.nlen[b] <= k1) return;
+  const cdf w = ((const cdf*)t.W0P)[((size_t)b * t.Nc + r) * 32 + lane];
+  float sigma, inv;
+  pow2_scale(warp_max(fmaxf(fabsf(w.re.hi), fabsf(w.im.hi))), sigma, inv);
+  float sr[kSlices], si[kSlices];
+  df_slices(df_scale(w.re, inv), sr);
+  df_slices(df_scale(w.im, inv), si);
+  __nv_bfloat16* A = z.A + (size_t)b * kSlices * z.KP * 64;
+#pragma unroll
+  for (int i = 0; i < kSlices; ++i) {
+    __nv_bfloat16* row = A + ((size_t)i * z.KP + r) * 64;
+    row[lane] = __float2bfloat16_rn(sr[i]);
+    row[32 + lane] = __float2bfloat16_rn(si[i]);
+  }
+  if (lane == 0) z.As[(size_t)b * z.KP + r] = sigma;
+}
+
+// B slices: trailing columns c of Bot (rows k0 .. k0+31 of the state).  Layout
+// [b][slice][re/im][TP][64] BF16 (row c), sigma_c in Bs[b][TP].
+__global__ void __launch_bounds__(256) oz_slice_b_kernel(StepArgs a, BlockedArgs t, OzArgs z, int64_t k0,
+                                                          int64_t k1) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;  // lane = row of the panel
+  const int64_t b = blockIdx.y;
+  const int64_t c = k1 + (int64_t)blockIdx.x * 8 + warp;
+  if (c >= t.Nc) return;
+  if (a.nlen && a.nlen[b] <= k1) return;
+  const int64_t Nc = t.Nc, Ncp = (Nc + 31) & ~(int64_t)31;
+  const cdf* W = (const cdf*)t.W + (size_t)b * Nc * Ncp;
+  const cdf v = W[((c >> 5) * Nc + k0 + lane) * 32 + (c & 31)];
+  float sigma, inv;
+  pow2_scale(warp_max(fmaxf(fabsf(v.re.hi), fabsf(v.im.hi))), sigma, inv);
+  float sr[kSlices], si[kSlices];
+  df_slices(df_scale(v.re, inv), sr);
+  df_slices(df_scale(v.im, inv), si);
+  __nv_bfloat16* B = z.B + (size_t)b * kSlices * 2 * z.TP * 64;
+#pragma unroll
+  for (int j = 0; j < kSlices; ++j) {
+    __nv_bfloat16* re_row = B + (((size_t)j * 2 + 0) * z.TP + c) * 64;  // [Re ; -Im]
+    __nv_bfloat16* im_row = B + (((size_t)j * 2 + 1) * z.TP + c) * 64;  // [Im ; Re]
+    re_row[lane] = __float2bfloat16_rn(sr[j]);
+    re_row[32 + lane] = __float2bfloat16_rn(-si[j]);
+    im_row[lane] = __float2bfloat16_rn(si[j]);
+    im_row[32 + lane] = __float2bfloat16_rn(sr[j]);
+  }
+  if (lane == 0) z.Bs[(size_t)b * z.TP + c] = sigma;
+}
+
+// Top = W0_T - W0_P Bot for 128 old rows of one sample, every trailing slab.
+__global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                        const __grid_constant__ CUtensorMap tmB, StepArgs a,
+                                                        BlockedArgs t, OzArgs z, int64_t k0, int64_t k1) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = blockIdx.y;
+  const int64_t mt = blockIdx.x;
+  if (a.nlen && a.nlen[b] <= k1) return;  // uniform over the CTA
+  const int64_t Nc = t.Nc;
+  const int n_tiles = (int)((Nc - k1 + NT - 1) / NT);
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (sbase - raw);
+  uint8_t* pstage = gbase + kABytes + kBStages * kBStage;
+  uint64_t* bars = (uint64_t*)(pstage + kPStage);
+  const uint32_t bar0 = smem_u32(bars);
+  const uint32_t a_full = bar0;
+  auto b_full = [&](int s) { return bar0 + 8u * (1 + s); };
+  auto b_empty = [&](int s) { return bar0 + 8u * (1 + kBStages + s); };
+  const uint32_t acc_full = bar0 + 8u * (1 + 2 * kBStages);
+  const uint32_t acc_empty = acc_full + 8u;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 3 + 2 * kBStages);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const uint32_t sA = sbase, sB = sbase + kABytes;
+
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    for (int s = 0; s < kBStages; ++s) {
+      mbar_init(b_full(s), 1);
+      mbar_init(b_empty(s), 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpiWarps);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: the A slices once, then the B slices of every slab
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+    mbar_arrive_expect_tx(a_full, kABytes);
+    for (int i = 0; i < kSlices; ++i)
+      tma_load_2d(sA + i * kATile, &tmA, a_full, 0, (int32_t)((b * kSlices + i) * z.KP + mt * MT));
+    int issued = 0;
+    for (int nt = 0; nt < n_tiles; ++nt) {
+      const int s = nt % kBStages;
+      if (nt >= kBStages && !mbar_wait(b_empty(s), ((nt / kBStages) - 1) & 1, abort_flag)) {
+        *abort_flag = 1;
+        set_status(a.status, FFS_E_TIMEOUT);
+        break;
+      }
+      const int32_t c0 = (int32_t)(k1 + (int64_t)nt * NT);
+      const uint32_t st = sB + s * kBStage;
+      mbar_arrive_expect_tx(b_full(s), kBStage);
+      for (int j = 0; j < kSlices; ++j)
+        for (int ri = 0; ri < 2; ++ri)
+          tma_load_2d(st + (j * 2 + ri) * kBTile, &tmB, b_full(s), 0,
+                      (int32_t)(((b * kSlices + j) * 2 + ri) * z.TP + c0));
+      ++issued;
+    }
+    // never leave with copies in flight
+    mbar_wait(a_full, 0, abort_flag);
+    for (int nt = (issued > kBStages ? issued - kBStages : 0); nt < issued; ++nt)
+      mbar_wait(b_full(nt % kBStages), (nt / kBStages) & 1, abort_flag);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: accumulator d of the real part at columns 32 (d-2), of the
+    // imaginary part at 32 (kNumD + d - 2)
+    bool ok = mbar_wait(a_full, 0, abort_flag);
+    if (!ok) {
+      *abort_flag = 1;
+      set_status(a.status, FFS_E_TIMEOUT);
+    }
+    for (int nt = 0; nt < n_tiles && ok; ++nt) {
+      const int s = nt % kBStages;
+      if (!mbar_wait(b_full(s), (nt / kBStages) & 1, abort_flag) ||
+          (nt >= 1 && !mbar_wait(acc_empty, (nt - 1) & 1, abort_flag))) {
+        *abort_flag = 1;
+        set_status(a.status, FFS_E_TIMEOUT);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = sB + s * kBStage;
+      for (int d = 2; d <= kDmax; ++d) {
+        bool first = true;
+        for (int i = 1; i <= kSlices; ++i) {
+          const int j = d - i;
+          if (j < 1 || j > kSlices) continue;
+          const uint32_t ta = sA + (i - 1) * kATile;
+          const uint32_t tre = st + ((j - 1) * 2 + 0) * kBTile, tim = st + ((j - 1) * 2 + 1) * kBTile;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t koff = kk * 32;
+            const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+            const uint64_t da = smem_desc_sw128(ta + koff);
+            mma_bf16(tmem + (uint32_t)(32 * (d - 2)), da, smem_desc_sw128(tre + koff), kIdesc, acc);
+            mma_bf16(tmem + (uint32_t)(32 * (kNumD + d - 2)), da, smem_desc_sw128(tim + koff), kIdesc, acc);
+          }
+          first = false;
+        }
+      }
+      mma_commit(b_empty(s));
+      mma_commit(acc_full);
+    }
+  } else if (warp >= 2) {
+    // ---- epilogue: thread = old row (its TMEM lane) and kEpiCols columns while reading
+    // the accumulators; then lanes over columns while updating W0_T, kEpiCols rows per warp
+    const int q = warp & 3;             // TMEM lane quarter
+    const int h = (warp - 2) >> 2;      // column group of the slab
+    const uint32_t quarter_bar = 1 + q; // the warps of a quarter
+    const uint32_t quarter_threads = 32 * (kEpiWarps / 4);
+    const int64_t j = mt * MT + 32 * q + lane;
+    const bool live_row = j < k0;
+    const float sr = live_row ? z.As[(size_t)b * z.KP + j] : 1.f;
+    const int64_t Ncp = (Nc + 31) & ~(int64_t)31;
+    uint8_t* Pq = pstage + (size_t)q * 32 * kPRow;  // the quarter's 32 rows
+    // All warps of a quarter pass the two quarter barriers of every slab even after a wait
+    // has failed (they then skip the work), so that none can be left at a barrier.
+    bool dead = false;
+    for (int nt = 0; nt < n_tiles; ++nt) {
+      const bool ok = !dead && mbar_wait(acc_full, nt & 1, abort_flag);
+      if (!ok && !dead) {
+        set_status(a.status, FFS_E_TIMEOUT);
+        *abort_flag = 1;
+        dead = true;
+      }
+      const int64_t c0 = k1 + (int64_t)nt * NT;
+      if (ok) tc_fence_after();
+      for (int part = 0; part < 2 && ok; ++part) {  // real, then imaginary part of the product
+        df S[kEpiCols];
+#pragma unroll
+        for (int n = 0; n < kEpiCols; ++n) S[n] = df{0.f, 0.f};
+        for (int d = kDmax; d >= 2; --d) {  // smallest terms first
+          uint32_t r[kEpiCols];
+          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * (part * kNumD + d - 2) + kEpiCols * h), r);
+          tmem_ld_wait();
+          const float p2 = ldexpf(1.f, -8 * (d - 2));
+#pragma unroll
+          for (int n = 0; n < kEpiCols; ++n) S[n] = df_add(S[n], df{__uint_as_float(r[n]) * p2, 0.f});
+        }
+#pragma unroll
+        for (int n = 0; n < kEpiCols; ++n) {
+          const int64_t c = c0 + kEpiCols * h + n;
+          const float scale = (c < Nc) ? sr * z.Bs[(size_t)b * z.TP + c] * 0x1p-14f : 0.f;
+          *(df*)(Pq + lane * kPRow + (kEpiCols * h + n) * 16 + part * 8) = df_scale(S[n], scale);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0 && ok) mbar_arrive(acc_empty);  // the accumulators may be overwritten now
+      named_sync(quarter_bar, quarter_threads);     // all the quarter's columns are staged
+      cdf* Wc = (cdf*)t.W + (size_t)b * Nc * Ncp + (size_t)(c0 >> 5) * Nc * 32;
+      const bool col_ok = ok && c0 + lane < Nc;
+#pragma unroll
+      for (int rr = kEpiCols * h; rr < kEpiCols * h + kEpiCols; ++rr) {
+        const int64_t jr = mt * MT + 32 * q + rr;
+        if (jr < k0 && col_ok) {
+          const cdf p = *(const cdf*)(Pq + rr * kPRow + lane * 16);
+          cdf w = Wc[jr * 32 + lane];
+          w.re = df_sub(w.re, p.re);
+          w.im = df_sub(w.im, p.im);
+          Wc[jr * 32 + lane] = w;
+        }
+      }
+      named_sync(quarter_bar, quarter_threads);  // before the next slab overwrites the staging rows
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+}  // namespace
+
+size_t oz_bytes_per_sample(int64_t Nc) {
+  const int64_t KP = (Nc + MT - 1) / MT * MT, TP = (Nc + NT - 1) / NT * NT;
+  return (size_t)kSlices * KP * 64 * 2 + (size_t)KP * 4 + (size_t)kSlices * 2 * TP * 64 * 2 + (size_t)TP * 4;
+}
+
+cudaError_t oz_prepare(ffs_ctx* c, int64_t Bw, int64_t Nc) {
+  const int64_t KP = (Nc + MT - 1) / MT * MT, TP = (Nc + NT - 1) / NT * NT;
+  const size_t need = (size_t)Bw * oz_bytes_per_sample(Nc);
+  if (need > c->oz_bytes) {
+    cudaFree(c->oz_buf);
+    c->oz_buf = nullptr;
+    c->oz_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->oz_buf, need);
+    if (e != cudaSuccess) return e;
+    c->oz_bytes = need;
+    c->oz_key_B = -1;
+  }
+  if (c->oz_key_B != Bw || c->oz_key_Nc != Nc) {
+    char* p = (char*)c->oz_buf;
+    c->oz.A = (__nv_bfloat16*)p;
+    p += (size_t)Bw * kSlices * KP * 64 * 2;
+    c->oz.B = (__nv_bfloat16*)p;
+    p += (size_t)Bw * kSlices * 2 * TP * 64 * 2;
+    c->oz.As = (float*)p;
+    p += (size_t)Bw * KP * 4;
+    c->oz.Bs = (float*)p;
+    c->oz.KP = KP;
+    c->oz.TP = TP;
+    cudaError_t e = encode_2d(&c->ozA, c->oz.A, false, 64, (uint64_t)Bw * kSlices * KP, kARows);
+    if (e == cudaSuccess) e = encode_2d(&c->ozB, c->oz.B, false, 64, (uint64_t)Bw * kSlices * 2 * TP, kBRows);
+    if (e != cudaSuccess) return e;
+    c->oz_key_B = Bw;
+    c->oz_key_Nc = Nc;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_oz_top(ffs_ctx* c, const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, int op,
+                          cudaStream_t s) {
+  if (k1 >= t.Nc || a.bw <= 0) return cudaSuccess;
+  const OzArgs z = c->oz;
+  if (k0 > 0) {
+    oz_slice_a_kernel<<<dim3((unsigned)((k0 + 7) / 8), (unsigned)a.bw), 256, 0, s>>>(a, t, z, k0, k1);
+    oz_slice_b_kernel<<<dim3((unsigned)((t.Nc - k1 + 7) / 8), (unsigned)a.bw), 256, 0, s>>>(a, t, z, k0, k1);
+    oz_top_kernel<<<dim3((unsigned)((k0 + MT - 1) / MT), (unsigned)a.bw), kThreads, kSmem, s>>>(c->ozA, c->ozB, a,
+                                                                                                t, z, k0, k1);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && op != kOpNone && k1 < a.n_steps) e = launch_column_operand(a, t, k1, kStateDF64, op, s);
+  return e;
+}
+
+cudaError_t configure_oz() {
+  return cudaFuncSetAttribute(oz_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+}
+
+}  // namespace fermi

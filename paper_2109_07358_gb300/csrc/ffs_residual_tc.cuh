@@ -25,5 +25,8 @@ cudaError_t prepare_residual_tc_bn(ffs_ctx* c, int op, int bn);
 // Column tile (128 or 256) for this size class: autotuned on first use, then cached.
 int residual_tile_for(ffs_ctx* c, const StepArgs& a, int op, cudaStream_t s);
 int residual_k_block(int op);    // K elements per 128-byte TMA row
+// Tensor map of a row-major rows x inner matrix (BF16, or FP32 when f32), boxes of 128
+// bytes x box_rows with the 128-byte swizzle.
+cudaError_t encode_2d(CUtensorMap* map, const void* base, bool f32, uint64_t inner, uint64_t rows, uint32_t box_rows);
 
 }  // namespace fermi

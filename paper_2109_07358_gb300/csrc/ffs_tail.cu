@@ -725,7 +725,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
     df* Wrs = Wrs_all + warp * 32;
     for (int e = tid; e < NB * 32; e += blockDim.x) Bsum[e] = df_add(Bs[e].re, Bs[e].im);
     __syncthreads();
-    for (int64_t j = warp; j < k0; j += 8) {
+    for (int64_t j = warp; j < (t.tc_top ? 0 : k0); j += 8) {
       if (lane < nbr) {
         const A wv = W0P[j * NB + lane];
         Wrow[lane] = wv;
@@ -776,7 +776,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   __syncthreads();
 
   // operand of step k1 (its column is the first of T)
-  if (op_mode != kOpNone && cb == 0 && k1 < a.n_steps) {
+  if (op_mode != kOpNone && cb == 0 && k1 < a.n_steps && !t.tc_top) {
     for (int64_t j = tid; j <= k1; j += blockDim.x) {
       const A v = (j < k1) ? T::neg(Wc[j * 32]) : T::one();  // column k1 = c0 (cb == 0)
       put_state<A>(a, op_mode, b, operand_col(a, mrow, j), v);
@@ -887,6 +887,33 @@ static cudaError_t group_panel_t(const GroupInst* inst, const GroupEntry* e, int
                                  cudaStream_t s) {
   panel_group_kernel<A><<<(unsigned)total, 256, panel_smem(sizeof(A)), s>>>(inst, e, n, op);
   return cudaGetLastError();
+}
+
+// Operand of step k1 from the state's column k1 (all rows updated): h = (-W[:, k1] ; 1).
+template <typename A>
+__global__ void column_operand_kernel(StepArgs a, BlockedArgs t, int64_t k1, int op_mode) {
+  using T = Ar<A>;
+  const int64_t b = blockIdx.x;
+  if (b >= a.bw || (a.nlen && a.nlen[b] <= k1)) return;
+  const int64_t Nc = t.Nc;
+  const A* W = (const A*)t.W + (size_t)b * state_stride(Nc);
+  const int32_t* mrow = a.m + b * a.N;
+  for (int64_t j = threadIdx.x; j <= k1; j += blockDim.x) {
+    const A v = (j < k1) ? T::neg(W[sidx(Nc, j, k1)]) : T::one();
+    put_state<A>(a, op_mode, b, operand_col(a, mrow, j), v);
+  }
+}
+
+template <typename A>
+static cudaError_t column_operand_t(const StepArgs& a, const BlockedArgs& t, int64_t k1, int op, cudaStream_t s) {
+  column_operand_kernel<A><<<(unsigned)a.bw, 128, 0, s>>>(a, t, k1, op);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_column_operand(const StepArgs& a, const BlockedArgs& t, int64_t k1, int state, int op,
+                                  cudaStream_t s) {
+  if (a.bw <= 0) return cudaSuccess;
+  return FFS_DISPATCH_STATE(a.cplx, state, column_operand_t, a, t, k1, op, s);
 }
 
 template <typename A>

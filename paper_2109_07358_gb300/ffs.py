@@ -37,6 +37,7 @@ FFS_FORM_GROUPED = 0x200
 FFS_GROUP_SIZE = 128
 FFS_NO_ORTHO_CHECK = 0x1000
 FFS_TAIL_UNBLOCKED = 0x2000
+FFS_TRAILING_TC = 0x4000
 
 _lib = None
 
@@ -225,8 +226,9 @@ def ffs_query(h, B: int = 0):
 
 
 FFS_PHASE_PERM, FFS_PHASE_RESIDUAL, FFS_PHASE_TAIL, FFS_PHASE_PANEL, FFS_PHASE_PANEL_S = 0, 1, 2, 3, 4
-FFS_NUM_PHASES = 5
-PHASE_NAMES = ("perm", "residual", "tail", "panel", "panel_s")
+FFS_PHASE_PANEL_TC = 5
+FFS_NUM_PHASES = 6
+PHASE_NAMES = ("perm", "residual", "tail", "panel", "panel_s", "panel_tc")
 
 
 def ffs_profile(h, enable: bool = True):
