@@ -6,7 +6,6 @@ Serving: requests submitted at different times (continuous batching, admission b
 device-memory budget) must each give exactly their standalone samples, whatever else
 shares the GPU with them.
 """
-import threading
 import time
 
 import numpy as np

@@ -12,7 +12,6 @@ within eps of an oracle CDF boundary between the two sites (eps = the mode's
 probability tolerance); for the modes with an accuracy target at least 99.9% of the
 10^4 chain samples (95% of the 70-sample cases) must be identical.
 """
-import math
 
 import numpy as np
 import pytest

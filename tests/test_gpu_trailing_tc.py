@@ -9,7 +9,6 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import ffs_oracle as orc
 from paper_2109_07358_gb300 import ffs
 from paper_2109_07358_gb300 import workloads as w
 from tests.parity_util import draw_identity, oracle_runs_parallel

@@ -4,7 +4,6 @@ run over the whole range exactly."""
 import os
 
 import numpy as np
-import pytest
 import torch
 import torch.multiprocessing as mp
 
