@@ -95,8 +95,9 @@ typedef enum {
  *   FFS_TRAILING_TC  opt-in: the once-per-panel update of the old rows' remaining columns
  *                    runs on the tensor cores through an error-free split of the
  *                    double-float operands into BF16 slices (products exact in FP32
- *                    accumulation, double-float epilogue).  Complex U, FFS_STATE_DF64 and
- *                    the blocked state only (else FFS_E_UNSUPPORTED at creation).
+ *                    accumulation, double-float epilogue).  FFS_STATE_DF64, the blocked
+ *                    state and a tensor-core residual only (else FFS_E_UNSUPPORTED at
+ *                    creation).
  * Checks:
  *   FFS_NO_ORTHO_CHECK  skip the U^dagger U = 1 check in ffs_create_ex
  */

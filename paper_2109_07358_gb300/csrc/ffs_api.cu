@@ -254,11 +254,11 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
   if (L > (int64_t)1 << 30) return fail(nullptr, FFS_E_ARG, "ffs_create_ex: L too large");
   const bool cplx = (dtype == FFS_C128 || dtype == FFS_C64);
   if ((flags & FFS_TRAILING_TC) &&
-      (!cplx || (flags & FFS_STATE_MASK) != FFS_STATE_DF64 || (flags & FFS_TAIL_UNBLOCKED) ||
+      ((flags & FFS_STATE_MASK) != FFS_STATE_DF64 || (flags & FFS_TAIL_UNBLOCKED) ||
        (flags & FFS_FORM_MASK) == FFS_FORM_PLAIN || (flags & FFS_RES_MASK) == FFS_RES_FP32))
     return fail(nullptr, FFS_E_UNSUPPORTED,
-                "ffs_create_ex: the tensor-core trailing update needs complex U, the double-float state, the "
-                "blocked state and a tensor-core residual");
+                "ffs_create_ex: the tensor-core trailing update needs the double-float state, the blocked "
+                "state and a tensor-core residual");
   if ((flags & FFS_FORM_MASK) == FFS_FORM_PLAIN)
     flags = (flags & ~(FFS_RES_MASK | FFS_STATE_MASK)) | FFS_RES_FP32 | FFS_STATE_FP32 | FFS_TAIL_UNBLOCKED;
   if ((flags & FFS_FORM_MASK) > FFS_FORM_GROUPED || (flags & FFS_STATE_MASK) > FFS_STATE_DF64 ||

@@ -1,4 +1,4 @@
-// Trailing update of the old rows on tensor cores (opt-in, complex double-float state).
+// Trailing update of the old rows on tensor cores (opt-in, double-float state).
 //
 // At a panel end the old rows' trailing columns take Top = W0_T - W0_P Bot (the
 // block-inverse identity of the blocked state, see ffs_tail.cu): per sample a
@@ -17,6 +17,7 @@
 //     accumulation is exact;
 //   * the epilogue adds the seven accumulators in double-float, scales by
 //     sigma_r sigma_c 2^(-14 - 8(d-2)) and subtracts from W0_T.
+// A real state uses the same kernels with [values | 0] rows and the real part only.
 // The dropped slice products (i + j > 8) are below 2^-46 of sigma_r sigma_c K, the order
 // of the double-float rounding of the direct update.
 //
@@ -82,7 +83,9 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Power-of-two scale sigma >= max, as (sigma, 1/sigma); 1 for an all-zero vector.
+// Power-of-two scale sigma >= max, as (sigma, 1/sigma); 1 for an all-zero vector.  A
+// subnormal max (localised orbitals leave rows of order 1e-40) takes sigma = 2^-125, so
+// that 1/sigma stays finite; v / sigma >= 2^-24 is then still exact in the 48 slice bits.
 __device__ __forceinline__ void pow2_scale(float mx, float& sigma, float& inv) {
   if (!(mx > 0.f)) {
     sigma = inv = 1.f;
@@ -90,13 +93,16 @@ __device__ __forceinline__ void pow2_scale(float mx, float& sigma, float& inv) {
   }
   int e;
   frexpf(mx, &e);  // mx = m 2^e, m in [0.5, 1): mx < 2^e
+  e = max(e, -125);
   sigma = ldexpf(1.f, e);
   inv = ldexpf(1.f, -e);
 }
 
 __device__ __forceinline__ df df_scale(df v, float p2) { return {v.hi * p2, v.lo * p2}; }  // exact (power of 2)
 
-// A slices: rows r < k0 of W0_P.  Layout [b][slice][KP][64] BF16, sigma_r in As[b][KP].
+// A slices: rows r < k0 of W0_P.  Layout [b][slice][KP][64] BF16, sigma_r in As[b][KP];
+// a complex row is [Re | Im], a real one [values | 0].
+template <bool CX>
 __global__ void __launch_bounds__(256) oz_slice_a_kernel(StepArgs a, BlockedArgs t, OzArgs z, int64_t k0,
                                                           int64_t k1) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -104,12 +110,19 @@ __global__ void __launch_bounds__(256) oz_slice_a_kernel(StepArgs a, BlockedArgs
   const int64_t r = (int64_t)blockIdx.x * 8 + warp;
   if (r >= k0) return;
   if (a.nlen && a.nlen[b] <= k1) return;
-  const cdf w = ((const cdf*)t.W0P)[((size_t)b * t.Nc + r) * 32 + lane];
+  df wre, wim = df{0.f, 0.f};
+  if constexpr (CX) {
+    const cdf w = ((const cdf*)t.W0P)[((size_t)b * t.Nc + r) * 32 + lane];
+    wre = w.re;
+    wim = w.im;
+  } else {
+    wre = ((const df*)t.W0P)[((size_t)b * t.Nc + r) * 32 + lane];
+  }
   float sigma, inv;
-  pow2_scale(warp_max(fmaxf(fabsf(w.re.hi), fabsf(w.im.hi))), sigma, inv);
+  pow2_scale(warp_max(fmaxf(fabsf(wre.hi), fabsf(wim.hi))), sigma, inv);
   float sr[kSlices], si[kSlices];
-  df_slices(df_scale(w.re, inv), sr);
-  df_slices(df_scale(w.im, inv), si);
+  df_slices(df_scale(wre, inv), sr);
+  df_slices(df_scale(wim, inv), si);
   __nv_bfloat16* A = z.A + (size_t)b * kSlices * z.KP * 64;
 #pragma unroll
   for (int i = 0; i < kSlices; ++i) {
@@ -121,7 +134,9 @@ __global__ void __launch_bounds__(256) oz_slice_a_kernel(StepArgs a, BlockedArgs
 }
 
 // B slices: trailing columns c of Bot (rows k0 .. k0+31 of the state).  Layout
-// [b][slice][re/im][TP][64] BF16 (row c), sigma_c in Bs[b][TP].
+// [b][slice][re/im][TP][64] BF16 (row c), sigma_c in Bs[b][TP]; a real column is
+// [values ; 0] in the first plane only.
+template <bool CX>
 __global__ void __launch_bounds__(256) oz_slice_b_kernel(StepArgs a, BlockedArgs t, OzArgs z, int64_t k0,
                                                           int64_t k1) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;  // lane = row of the panel
@@ -130,27 +145,37 @@ __global__ void __launch_bounds__(256) oz_slice_b_kernel(StepArgs a, BlockedArgs
   if (c >= t.Nc) return;
   if (a.nlen && a.nlen[b] <= k1) return;
   const int64_t Nc = t.Nc, Ncp = (Nc + 31) & ~(int64_t)31;
-  const cdf* W = (const cdf*)t.W + (size_t)b * Nc * Ncp;
-  const cdf v = W[((c >> 5) * Nc + k0 + lane) * 32 + (c & 31)];
+  const size_t idx = (size_t)b * Nc * Ncp + ((c >> 5) * Nc + k0 + lane) * 32 + (c & 31);
+  df vre, vim = df{0.f, 0.f};
+  if constexpr (CX) {
+    const cdf v = ((const cdf*)t.W)[idx];
+    vre = v.re;
+    vim = v.im;
+  } else {
+    vre = ((const df*)t.W)[idx];
+  }
   float sigma, inv;
-  pow2_scale(warp_max(fmaxf(fabsf(v.re.hi), fabsf(v.im.hi))), sigma, inv);
+  pow2_scale(warp_max(fmaxf(fabsf(vre.hi), fabsf(vim.hi))), sigma, inv);
   float sr[kSlices], si[kSlices];
-  df_slices(df_scale(v.re, inv), sr);
-  df_slices(df_scale(v.im, inv), si);
+  df_slices(df_scale(vre, inv), sr);
+  df_slices(df_scale(vim, inv), si);
   __nv_bfloat16* B = z.B + (size_t)b * kSlices * 2 * z.TP * 64;
 #pragma unroll
   for (int j = 0; j < kSlices; ++j) {
     __nv_bfloat16* re_row = B + (((size_t)j * 2 + 0) * z.TP + c) * 64;  // [Re ; -Im]
-    __nv_bfloat16* im_row = B + (((size_t)j * 2 + 1) * z.TP + c) * 64;  // [Im ; Re]
     re_row[lane] = __float2bfloat16_rn(sr[j]);
     re_row[32 + lane] = __float2bfloat16_rn(-si[j]);
-    im_row[lane] = __float2bfloat16_rn(si[j]);
-    im_row[32 + lane] = __float2bfloat16_rn(sr[j]);
+    if constexpr (CX) {
+      __nv_bfloat16* im_row = B + (((size_t)j * 2 + 1) * z.TP + c) * 64;  // [Im ; Re]
+      im_row[lane] = __float2bfloat16_rn(si[j]);
+      im_row[32 + lane] = __float2bfloat16_rn(sr[j]);
+    }
   }
   if (lane == 0) z.Bs[(size_t)b * z.TP + c] = sigma;
 }
 
 // Top = W0_T - W0_P Bot for 128 old rows of one sample, every trailing slab.
+template <bool CX>
 __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_constant__ CUtensorMap tmA,
                                                         const __grid_constant__ CUtensorMap tmB, StepArgs a,
                                                         BlockedArgs t, OzArgs z, int64_t k0, int64_t k1) {
@@ -213,9 +238,9 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
       }
       const int32_t c0 = (int32_t)(k1 + (int64_t)nt * NT);
       const uint32_t st = sB + s * kBStage;
-      mbar_arrive_expect_tx(b_full(s), kBStage);
+      mbar_arrive_expect_tx(b_full(s), CX ? kBStage : kBStage / 2);
       for (int j = 0; j < kSlices; ++j)
-        for (int ri = 0; ri < 2; ++ri)
+        for (int ri = 0; ri < (CX ? 2 : 1); ++ri)
           tma_load_2d(st + (j * 2 + ri) * kBTile, &tmB, b_full(s), 0,
                       (int32_t)(((b * kSlices + j) * 2 + ri) * z.TP + c0));
       ++issued;
@@ -256,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
             const uint32_t acc = (first && kk == 0) ? 0u : 1u;
             const uint64_t da = smem_desc_sw128(ta + koff);
             mma_bf16(tmem + (uint32_t)(32 * (d - 2)), da, smem_desc_sw128(tre + koff), kIdesc, acc);
-            mma_bf16(tmem + (uint32_t)(32 * (kNumD + d - 2)), da, smem_desc_sw128(tim + koff), kIdesc, acc);
+            if (CX) mma_bf16(tmem + (uint32_t)(32 * (kNumD + d - 2)), da, smem_desc_sw128(tim + koff), kIdesc, acc);
           }
           first = false;
         }
@@ -288,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
       }
       const int64_t c0 = k1 + (int64_t)nt * NT;
       if (ok) tc_fence_after();
-      for (int part = 0; part < 2 && ok; ++part) {  // real, then imaginary part of the product
+      for (int part = 0; part < (CX ? 2 : 1) && ok; ++part) {  // real, then imaginary part of the product
         df S[kEpiCols];
 #pragma unroll
         for (int n = 0; n < kEpiCols; ++n) S[n] = df{0.f, 0.f};
@@ -311,17 +336,23 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
       __syncwarp();
       if (lane == 0 && ok) mbar_arrive(acc_empty);  // the accumulators may be overwritten now
       named_sync(quarter_bar, quarter_threads);     // all the quarter's columns are staged
-      cdf* Wc = (cdf*)t.W + (size_t)b * Nc * Ncp + (size_t)(c0 >> 5) * Nc * 32;
+      const size_t slab = (size_t)b * Nc * Ncp + (size_t)(c0 >> 5) * Nc * 32;
       const bool col_ok = ok && c0 + lane < Nc;
 #pragma unroll
       for (int rr = kEpiCols * h; rr < kEpiCols * h + kEpiCols; ++rr) {
         const int64_t jr = mt * MT + 32 * q + rr;
         if (jr < k0 && col_ok) {
           const cdf p = *(const cdf*)(Pq + rr * kPRow + lane * 16);
-          cdf w = Wc[jr * 32 + lane];
-          w.re = df_sub(w.re, p.re);
-          w.im = df_sub(w.im, p.im);
-          Wc[jr * 32 + lane] = w;
+          if constexpr (CX) {
+            cdf* Wc = (cdf*)t.W + slab;
+            cdf w = Wc[jr * 32 + lane];
+            w.re = df_sub(w.re, p.re);
+            w.im = df_sub(w.im, p.im);
+            Wc[jr * 32 + lane] = w;
+          } else {
+            df* Wc = (df*)t.W + slab;
+            Wc[jr * 32 + lane] = df_sub(Wc[jr * 32 + lane], p.re);
+          }
         }
       }
       named_sync(quarter_bar, quarter_threads);  // before the next slab overwrites the staging rows
@@ -380,10 +411,17 @@ cudaError_t launch_oz_top(ffs_ctx* c, const StepArgs& a, const BlockedArgs& t, i
   if (k1 >= t.Nc || a.bw <= 0) return cudaSuccess;
   const OzArgs z = c->oz;
   if (k0 > 0) {
-    oz_slice_a_kernel<<<dim3((unsigned)((k0 + 7) / 8), (unsigned)a.bw), 256, 0, s>>>(a, t, z, k0, k1);
-    oz_slice_b_kernel<<<dim3((unsigned)((t.Nc - k1 + 7) / 8), (unsigned)a.bw), 256, 0, s>>>(a, t, z, k0, k1);
-    oz_top_kernel<<<dim3((unsigned)((k0 + MT - 1) / MT), (unsigned)a.bw), kThreads, kSmem, s>>>(c->ozA, c->ozB, a,
-                                                                                                t, z, k0, k1);
+    const dim3 ga((unsigned)((k0 + 7) / 8), (unsigned)a.bw), gb((unsigned)((t.Nc - k1 + 7) / 8), (unsigned)a.bw);
+    const dim3 gt((unsigned)((k0 + MT - 1) / MT), (unsigned)a.bw);
+    if (a.cplx) {
+      oz_slice_a_kernel<true><<<ga, 256, 0, s>>>(a, t, z, k0, k1);
+      oz_slice_b_kernel<true><<<gb, 256, 0, s>>>(a, t, z, k0, k1);
+      oz_top_kernel<true><<<gt, kThreads, kSmem, s>>>(c->ozA, c->ozB, a, t, z, k0, k1);
+    } else {
+      oz_slice_a_kernel<false><<<ga, 256, 0, s>>>(a, t, z, k0, k1);
+      oz_slice_b_kernel<false><<<gb, 256, 0, s>>>(a, t, z, k0, k1);
+      oz_top_kernel<false><<<gt, kThreads, kSmem, s>>>(c->ozA, c->ozB, a, t, z, k0, k1);
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && op != kOpNone && k1 < a.n_steps) e = launch_column_operand(a, t, k1, kStateDF64, op, s);
@@ -391,7 +429,10 @@ cudaError_t launch_oz_top(ffs_ctx* c, const StepArgs& a, const BlockedArgs& t, i
 }
 
 cudaError_t configure_oz() {
-  return cudaFuncSetAttribute(oz_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  cudaError_t e = cudaFuncSetAttribute(oz_top_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(oz_top_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  return e;
 }
 
 }  // namespace fermi

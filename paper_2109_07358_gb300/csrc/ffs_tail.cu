@@ -752,7 +752,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   } else if constexpr (std::is_same<A, df>::value) {
     // old rows with a lazy accumulator, the warp's W0_P row staged in shared memory
     A* Wrow = Wrow_all + warp * 32;
-    for (int64_t j = warp; j < k0; j += 8) {
+    for (int64_t j = warp; j < (t.tc_top ? 0 : k0); j += 8) {
       if (lane < nbr) Wrow[lane] = W0P[j * NB + lane];
       __syncwarp();
       lzf S1{0.f, 0.f};
@@ -764,7 +764,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
       for (int jn = warp; jn < nbr; jn += 8) Wc[(k0 + jn) * 32 + lane] = Bs[jn * 32 + lane];
   } else if (cval) {
     // old rows: Top = W0_T - W0_P Bot
-    for (int64_t j = warp; j < k0; j += 8) {
+    for (int64_t j = warp; j < (t.tc_top ? 0 : k0); j += 8) {
       A v = Wc[j * 32 + lane];
       const A* wp = W0P + j * NB;
       for (int ii = 0; ii < nbr; ++ii) v = T::fms(v, wp[ii], Bs[ii * 32 + lane]);

@@ -4,7 +4,7 @@ within double-float rounding.  The conditionals (FP32 outputs of a BF16x3 residu
 operand split can move by one BF16 unit when the state moves by a rounding) then agree
 with the direct path to 1e-7 and with the oracle within the chosen form's 1e-4; cases cover one and several 128-row
 tiles of old rows, ragged trailing slabs, L-ensemble chains that end inside panels, the
-grouped form, and the full-size lattice."""
+grouped form, real and complex states, and the full-size lattice."""
 import numpy as np
 import pytest
 import torch
@@ -22,6 +22,8 @@ CASES = {
     "panels": lambda: w.haar(160, 75, seed=9),            # two panel ends, k0 < 128
     "tiles": lambda: w.haar(1000, 300, seed=12),          # k0 up to 256: two row tiles, ragged slabs
     "lattice": lambda: w.square_lattice(16, 16, 100, seed=3),
+    "real_tiles": lambda: w.haar(1000, 300, seed=13, complex_=False),
+    "anderson": lambda: w.anderson_chain(2048, 200, 1.0, seed=2),
 }
 
 
@@ -110,10 +112,10 @@ def test_full_size_lattice():
 
 
 def test_unsupported_combinations():
-    Ur = torch.from_numpy(w.haar(64, 40, seed=1, complex_=False)).cuda()
     Uc = torch.from_numpy(w.haar(64, 40, seed=1)).cuda()
-    for U, flags in ((Ur, TC), (Uc, ffs.FFS_RES_BF16X3 | ffs.FFS_STATE_FP64 | ffs.FFS_TRAILING_TC),
-                     (Uc, ffs.FFS_RES_FP32 | ffs.FFS_STATE_DF64 | ffs.FFS_TRAILING_TC)):
+    for U, flags in ((Uc, ffs.FFS_RES_BF16X3 | ffs.FFS_STATE_FP64 | ffs.FFS_TRAILING_TC),
+                     (Uc, ffs.FFS_RES_FP32 | ffs.FFS_STATE_DF64 | ffs.FFS_TRAILING_TC),
+                     (Uc, TC | ffs.FFS_TAIL_UNBLOCKED)):
         with pytest.raises(ffs.FFSError) as e:
             ffs.Sampler(U, flags)
         assert e.value.code == ffs.FFS_E_UNSUPPORTED
