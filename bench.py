@@ -9,7 +9,9 @@ draw + state-update steps) over one batch of B samples of the workload.
 Default workload: 64 x 64 open square lattice with random U(1) hopping phases
 (L = 4096), the N = 1024 lowest orbitals (complex), B = 4096 samples, seed 0.
 Prints one JSON line (rank 0).  Under torchrun each rank samples its own index
-range (weak scaling, no collective on the data path).
+range (weak scaling, no collective on the data path).  Each timed step has its own
+CUDA events (their sum is the step time; p50/p99 per call come from them); a workload
+whose working set fits in L2 gets the cache flushed between steps, outside the events.
 """
 from __future__ import annotations
 
@@ -55,6 +57,16 @@ WORKLOADS = {
 # clock (FP64: 1.25 TFLOP/s dense nominal; FP32: 152 SMs x 128 lanes x 2 flops x 2.07 GHz).
 NOMINAL_FP64_TFLOPS = 1.25
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+L2_BYTES = 129 * 2**20
+
+
+def working_set_bytes(L, N, B, cplx, state):
+    """Bytes one step touches: the per-sample blocked state (N x round_up(N, 32) entries),
+    U in FP64 and its BF16 hi/lo copies, the output rows."""
+    entry = {"df64": 8, "fp64": 8, "fp32": 4}[state] * (2 if cplx else 1)
+    ncp = (N + 31) // 32 * 32
+    u = L * N * (2 if cplx else 1) * (8 + 4)
+    return B * N * ncp * entry + u + B * N * 4
 
 
 def load_peaks():
@@ -233,6 +245,14 @@ def oracle_baseline(U, n_samples, seed=0, workers=None):
                 os.environ[v] = old
 
 
+def oracle_sample_size(U, B, target_s=10.0):
+    """Samples of the workload to time the oracle on: one probe of one sample per core,
+    then as many as take about target_s of wall time on the same cores, at most B."""
+    n0 = max(2, os.cpu_count() or 1)
+    rate, _, _ = oracle_baseline(U, n0)
+    return int(min(max(n0, rate * target_s), max(n0, B)))
+
+
 def _oracle_pool(jobs, workers, n_samples):
     import multiprocessing as mp
 
@@ -250,7 +270,7 @@ def run_reference(args, spec, rank, world):
     if rank != 0:
         return 0
     U = make_U(spec)
-    n = args.ref_samples or max(2, (os.cpu_count() or 1))
+    n = args.ref_samples or oracle_sample_size(U, spec["B"])
     for _ in range(args.warmup):
         oracle_baseline(U, max(1, n // 4))
     rates = []
@@ -583,21 +603,28 @@ def main():
     for i in range(args.warmup):
         step(i)
     S.sync()
+    # a working set that fits in L2 twice over is evicted between timed steps by writing a
+    # buffer larger than L2, outside the per-step events; otherwise the steps run back to
+    # back and each step's inputs are larger than L2 already
+    ws = working_set_bytes(L, N, B, cplx, args.state)
+    flush = torch.empty(4 * L2_BYTES // 4, dtype=torch.int32, device="cuda") if ws < 2 * L2_BYTES else None
     ffs.ffs_profile(S.h, True)
     barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         torch.cuda.nvtx.range_push("timed")   # lets a profiler capture the timed steps only
-        ev0.record(stream)
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            step(args.warmup + i)
-        ev1.record(stream)
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                if flush is not None:
+                    flush.fill_(i)
+                evs[i][0].record(stream)
+                step(args.warmup + i)
+                evs[i][1].record(stream)
         S.sync()
-        wall = time.perf_counter() - t0
         torch.cuda.nvtx.range_pop()
     barrier()
-    ms_total = ev0.elapsed_time(ev1)
+    step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+    ms_total = float(step_ms.sum())
     prof = ffs.ffs_profile_read(S.h)
     ffs.ffs_profile(S.h, False)
     if dist is not None:
@@ -677,8 +704,12 @@ def main():
         "config": {"workload": args.workload, "desc": spec["desc"], "L": L, "N": N, "B": B,
                    "form": f"batched {args.chosen} residual + {args.state} state" +
                            (" + tensor-core trailing update" if flags & ffs.FFS_TRAILING_TC else ""),
-                   "l2": "inputs larger than L2 "
-                   "(the per-sample state of a batch is tens of GB)"},
+                   "working_set_bytes": ws,
+                   "l2": "inputs larger than L2 (steps back to back)" if flush is None else
+                   "working set below L2: a 516 MB buffer is written between timed steps, outside their "
+                   "CUDA events"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "calls": int(args.steps), "what": "one ffs_sample_ex call of B samples (CUDA events)"},
         "clocks": clk.summary(),
         "gpu_launches": prof_launches,
         "roofline": roof,
@@ -702,7 +733,7 @@ def main():
         P.close()
 
     if not args.no_cpu and rank == 0:
-        n = max(2, os.cpu_count() or 1)
+        n = oracle_sample_size(U_np, B)
         rate, wall, workers = oracle_baseline(U_np, n)
         out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": workers, "kind": "oracle",
                                "sample": f"{n} samples of the same workload (indices 0..{n - 1}), "

@@ -1,0 +1,50 @@
+"""Host-side logic of bench.py that needs no GPU: the oracle arm (--impl reference) prints
+the contract's JSON line, ranks other than 0 exit without work, and the L2 policy picks
+flushing exactly for the workloads whose working set fits in L2."""
+import json
+import os
+import subprocess
+import sys
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(extra_env, *args):
+    env = dict(os.environ, **extra_env)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_line():
+    p = _run({}, "--impl", "reference", "--workload", "chain64_N8_B10000", "--steps", "2", "--warmup", "0",
+             "--ref-samples", "64")
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == "FFS samples/s" and d["unit"] == "samples/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 2 and d["n_gpus"] == 1
+    assert d["config"]["workload"] == "chain64_N8_B10000" and d["config"]["B_per_step"] == 64
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "samples/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_do_nothing():
+    p = _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"}, "--impl", "reference", "--workload",
+             "chain64_N8_B10000", "--steps", "1", "--warmup", "0", "--ref-samples", "16")
+    assert p.returncode == 0, p.stderr[-2000:]
+    assert not [l for l in p.stdout.splitlines() if l.startswith("{")]
+
+
+def test_l2_policy():
+    flushed = {k for k, s in bench.WORKLOADS.items()
+               if bench.working_set_bytes(s["L"], s["N"], s["B"], s["cplx"], "df64") < 2 * bench.L2_BYTES}
+    assert flushed == {"chain64_N8_B10000"}
+    # the 64x64 lattice: 4096 samples x 1024 x 1024 complex double-float entries
+    s = bench.WORKLOADS["lattice64x64_N1024_B4096"]
+    assert bench.working_set_bytes(s["L"], s["N"], s["B"], s["cplx"], "df64") > 4096 * 1024 * 1024 * 16
