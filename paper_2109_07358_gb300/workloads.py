@@ -227,7 +227,9 @@ def double_well(L: int = 64, N: int = 4, c: float = 89.929, a: float = 4096.0, b
                 t: float = math.pi**2 / 6) -> np.ndarray:
     """Lowest-N orbitals of H = -t sum (c_i^+ c_{i+1} + h.c.) + sum_i V(x_i) n_i with
     V(x) = a (x^2 - b)^2 - c x and x_i evenly spaced on [-2, 2] (supplementary
-    double-well section)."""
+    double-well section).  The section quotes the balanced-to-imbalanced transition at
+    c = 89.929; with t as the nearest-neighbour element on these points it falls at
+    c = 46.645, so the default c is in the imbalanced stage."""
     xs = np.linspace(-2.0, 2.0, L)
     V = a * (xs**2 - b) ** 2 - c * xs
     H = np.diag(V) - t * (np.eye(L, k=1) + np.eye(L, k=-1))
