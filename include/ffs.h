@@ -97,7 +97,8 @@ typedef enum {
  *                    double-float operands into BF16 slices (products exact in FP32
  *                    accumulation, double-float epilogue).  FFS_STATE_DF64, the blocked
  *                    state and a tensor-core residual only (else FFS_E_UNSUPPORTED at
- *                    creation).
+ *                    creation).  It pays for complex U; for real U half of each slice
+ *                    row is zero padding and the direct update is as fast or faster.
  * Checks:
  *   FFS_NO_ORTHO_CHECK  skip the U^dagger U = 1 check in ffs_create_ex
  */
