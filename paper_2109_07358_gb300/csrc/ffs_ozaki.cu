@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
       }
       tc_fence_after();
       const uint32_t st = sB + s * kBStage;
+#pragma unroll 1  // unrolled, the 42 slice pairs' descriptors spill in the real kernel
       for (int d = 2; d <= kDmax; ++d) {
         bool first = true;
         for (int i = 1; i <= kSlices; ++i) {
