@@ -22,7 +22,7 @@ Method (main text around Eq. 2 and Eq. 3, Supplementary Section S-1):
   4. the inner products u_y^T h for all sites y give the weights (Section S-1: the
      2Lk operations of step k).
 
-Readings of points the paper leaves open (each is listed in the design notes):
+Readings of points the paper leaves open:
   * m is drawn per sample (the identity of Eq. 2 averages over all permutations;
     a fixed column order is biased).
   * The normal vector is h = (h_1..h_{k-1}, 1): its normalisation cancels in the
@@ -38,6 +38,29 @@ Readings of points the paper leaves open (each is listed in the design notes):
     0, 1) and i = N-2-2j (words 2, 3), each taking r = word_a * 2^32 + word_b and
     swapping m[i] with m[(r * (i+1)) >> 64].  Stream 1 block k gives the uniform of
     step k (0-based): u = ((w0 >> 5) * 2^26 + (w1 >> 6)) * 2^-53.
+
+What pins each part (none compares the oracle with itself):
+  * philox4x32_10: the published known-answer vectors (tests/golden).
+  * permutation, site_uniform: uniformity over S_4 (chi-squared), the N = 1 and N = 2
+    shuffles worked out by hand, 53-bit uniforms in [0, 1) (Kolmogorov-Smirnov).
+  * inverse_cdf: hand-made edge cases (zero weights, boundaries, the largest uniform,
+    the rounding fallback).
+  * sample_one / chain_probability: Eq. 2 by exact enumeration (the average over all N!
+    column orders equals |det U_x|^2 / N! for every ordered x, real and complex); the
+    conditional of every step against its determinant definition; the prefix marginal
+    (N-k)!/N! det K_XX of marginal sampling; per-step invariants (Z = |h|^2, zero weight
+    on drawn sites, prod |s_k|^2 = |det U_x|^2); N = 1 (Born rule), N = L, U = [I; 0]
+    (uniform orders); block-diagonal U (independent blocks); brute force over the 495
+    sets of the 12-site chain (chi-squared); one-body and pair densities; the double
+    well's deterministic stages and its Bernoulli case.  Planted slips (a transposed
+    operand, a sign, >= in the draw, an off-by-one shuffle) fail these pins.
+  * the L-ensemble, Metropolis and reweighting functions further down: pinned in their
+    own test files (brute-force subset laws, the exact short-chain transition law,
+    exact enumeration of small Anderson-Hubbard systems).
+  * sample, sample_parallel: loops over sample_one (no arithmetic of their own).
+  * target_ordered, conditional_by_determinants, set_probabilities, one_body_density,
+    pair_density: the definitions written out (determinants, K = U U^dagger); the tests
+    cross-check them with independent determinant loops and Cauchy-Binet.
 """
 from __future__ import annotations
 
