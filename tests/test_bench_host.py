@@ -48,3 +48,21 @@ def test_l2_policy():
     # the 64x64 lattice: 4096 samples x 1024 x 1024 complex double-float entries
     s = bench.WORKLOADS["lattice64x64_N1024_B4096"]
     assert bench.working_set_bytes(s["L"], s["N"], s["B"], s["cplx"], "df64") > 4096 * 1024 * 1024 * 16
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    import socket
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    p = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--workload", "chain64_N8_B10000", "--steps", "1",
+                        "--warmup", "0", "--ref-samples", "16"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
