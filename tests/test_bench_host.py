@@ -1,6 +1,7 @@
 """Host-side logic of bench.py that needs no GPU: the oracle arm (--impl reference) prints
-the contract's JSON line, ranks other than 0 exit without work, and the L2 policy picks
-flushing exactly for the workloads whose working set fits in L2."""
+the contract's JSON line, ranks other than 0 exit without work (also under a two-rank
+torchrun launch, which prints exactly one line), and the L2 policy picks flushing exactly
+for the workloads whose working set fits in L2."""
 import json
 import os
 import subprocess
