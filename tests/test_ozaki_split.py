@@ -1,0 +1,151 @@
+"""The arithmetic argument of the tensor-core trailing update, checked on the CPU with
+exact rationals.  The scheme (Ozaki, Ogita, Oishi & Rump 2012) as the kernels use it:
+a double-float value x (a pair of FP32 numbers) scaled by a power of two sigma >= |x| is
+cut into six 8-bit integer slices by FP32 arithmetic (round to nearest integer, exact
+remainder by an error-free sum, multiply by 256); the products of slices a_i b_j with
+i + j <= 8 are accumulated per d = i + j in FP32 over K = 64.  The claims:
+
+* every slice is an integer with |a_i| <= 128, so it is exact in BF16;
+* the six slices and the remainder add up to x / sigma exactly, and the remainder is
+  below 2^-48;
+* every FP32 partial sum of one accumulator is an integer below 2^23 (so the tensor-core
+  accumulation is exact whatever its order);
+* the dropped products (i + j > 8) and the remainders together stay below
+  2^-46 sigma_r sigma_c K of the exact product;
+* a subnormal maximum takes sigma = 2^-125 and its slices stay finite and exact.
+
+The slicing below is an FP32 restatement of the same steps (numpy float32 rounds to
+nearest even like the kernels' _rn operations); the expected values are exact rationals.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+F = np.float32
+SLICES, DMAX, K = 6, 8, 64
+
+
+def two_sum(a, b):
+    s = F(a + b)
+    bb = F(s - a)
+    e = F(F(a - F(s - bb)) + F(b - bb))
+    return s, e
+
+
+def pow2_scale(mx):
+    if not mx > 0:
+        return F(1.0), F(1.0)
+    _, e = np.frexp(F(mx))
+    e = max(int(e), -125)
+    return F(np.ldexp(1.0, e)), F(np.ldexp(1.0, -e))
+
+
+def slices(hi, lo):
+    th, tl = F(hi * F(128)), F(lo * F(128))
+    out = []
+    for _ in range(SLICES):
+        a = F(np.rint(th))
+        assert F(th - a) + a == th                     # th - a is exact
+        rh, rl = two_sum(F(th - a), tl)
+        out.append(a)
+        th, tl = F(rh * F(256)), F(rl * F(256))
+    return out, Fraction(float(th)) + Fraction(float(tl))  # remainder (scaled by 2^55)
+
+
+def random_df(rng, n, scale=1.0):
+    hi = (rng.standard_normal(n) * scale).astype(F)
+    lo = (rng.standard_normal(n) * np.abs(hi) * 2.0**-25).astype(F)
+    return hi, lo
+
+
+def exact(hi, lo):
+    return Fraction(float(hi)) + Fraction(float(lo))
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-20, 1e20])
+def test_slices_are_exact_bf16_integers_and_sum_to_x(scale):
+    rng = np.random.default_rng(1)
+    hi, lo = random_df(rng, 64, scale)
+    sigma, inv = pow2_scale(float(np.max(np.abs(hi))))
+    assert sigma >= np.max(np.abs(hi))
+    for h, l in zip(hi, lo):
+        s, rem = slices(F(h * inv), F(l * inv))
+        for a in s:
+            assert float(a).is_integer() and abs(a) <= 128    # 8 bits and a sign: exact in BF16
+        recon = sum(Fraction(int(a)) * Fraction(1, 2 ** (7 + 8 * i)) for i, a in enumerate(s))
+        remainder = rem * Fraction(1, 2 ** (7 + 8 * SLICES))
+        x = exact(F(h * inv), F(l * inv))
+        assert recon + remainder == x                          # an exact decomposition
+        assert abs(remainder) <= Fraction(1, 2 ** 48)
+
+
+def _split_matrix(hi, lo, axis):
+    """Per row (axis=1) or column (axis=0) power-of-two scales and slices (integers)."""
+    mx = np.max(np.abs(hi), axis=axis)
+    n = hi.shape[1 - axis]
+    sig = np.zeros(n, object)
+    S = np.zeros((SLICES,) + hi.shape, np.int64)
+    for r in range(n):
+        sg, inv = pow2_scale(float(mx[r]))
+        sig[r] = Fraction(float(sg))
+        idx = (r, slice(None)) if axis == 1 else (slice(None), r)
+        for q, (h, l) in enumerate(zip(hi[idx], lo[idx])):
+            s, _ = slices(F(h * inv), F(l * inv))
+            for i in range(SLICES):
+                if axis == 1:
+                    S[i, r, q] = int(s[i])
+                else:
+                    S[i, q, r] = int(s[i])
+    return S, sig
+
+
+def test_product_accumulators_are_exact_and_truncation_is_bounded():
+    rng = np.random.default_rng(2)
+    M, T = 6, 5
+    Ah, Al = random_df(rng, M * K)
+    Bh, Bl = random_df(rng, K * T)
+    Ah, Al, Bh, Bl = Ah.reshape(M, K), Al.reshape(M, K), Bh.reshape(K, T), Bl.reshape(K, T)
+    Ah[2] *= F(1e-30)                                           # rows and columns of very
+    Al[2] *= F(1e-30)                                           # different magnitudes
+    Bh[:, 1] *= F(1e12)
+    Bl[:, 1] *= F(1e12)
+    SA, sr = _split_matrix(Ah, Al, axis=1)
+    SB, sc = _split_matrix(Bh, Bl, axis=0)
+    for r in range(M):
+        for c in range(T):
+            acc = Fraction(0)
+            for d in range(2, DMAX + 1):
+                part = 0
+                for i in range(1, SLICES + 1):
+                    j = d - i
+                    if 1 <= j <= SLICES:
+                        for k in range(K):                     # any accumulation order
+                            part += int(SA[i - 1, r, k]) * int(SB[j - 1, k, c])
+                            assert abs(part) < 2 ** 23        # FP32 holds it exactly
+                acc += Fraction(part) * Fraction(1, 2 ** (14 + 8 * (d - 2)))
+            got = acc * sr[r] * sc[c]
+            want = sum(exact(Ah[r, k], Al[r, k]) * exact(Bh[k, c], Bl[k, c]) for k in range(K))
+            assert abs(got - want) <= Fraction(1, 2 ** 46) * sr[r] * sc[c] * K
+
+
+def test_worst_case_partial_sum_is_below_2_23():
+    # the most slice pairs share d = 7 (six pairs); all slices at their bound 128
+    pairs = max(sum(1 for i in range(1, SLICES + 1) if 1 <= d - i <= SLICES) for d in range(2, DMAX + 1))
+    assert pairs == 6
+    assert pairs * K * 128 * 128 < 2 ** 23
+
+
+def test_subnormal_row_maximum_keeps_finite_exact_slices():
+    hi = np.array([F(3e-40), F(-1e-41), F(0.0)], F)           # FP32 subnormals
+    assert np.all(np.abs(hi[:2]) < np.finfo(F).tiny)
+    sigma, inv = pow2_scale(float(np.max(np.abs(hi))))
+    assert sigma == F(2.0**-125) and np.isfinite(inv)
+    for h in hi:
+        s, rem = slices(F(h * inv), F(0.0))
+        recon = sum(Fraction(int(a)) * Fraction(1, 2 ** (7 + 8 * i)) for i, a in enumerate(s))
+        assert recon + rem * Fraction(1, 2 ** (7 + 8 * SLICES)) == Fraction(float(h)) / Fraction(float(sigma))
+    # without the clamp the inverse scale of a subnormal maximum overflows
+    _, e = np.frexp(F(3e-40))
+    with np.errstate(over="ignore"):
+        assert not np.isfinite(F(np.ldexp(F(1.0), -int(e))))
