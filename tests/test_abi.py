@@ -121,3 +121,24 @@ def test_noalloc_argument_checks(libpath):
     # a working set beyond the fixed array: B (8 N^2 + 4 L + 8 N) bytes and more
     assert L.ffs_sample_noalloc(p, C128, 1 << 20, 64, 4096, 0, px, None) == ffs.FFS_E_NOMEM
     assert b"working memory" in L.ffs_last_error(None)
+
+
+def test_no_cpu_fallback_without_a_gpu(libpath):
+    """On a machine without a usable GPU the product path refuses with FFS_E_CUDA: there
+    is no CPU fallback for a sampler or for the allocation-free entry point."""
+    import numpy as np
+    import torch
+
+    from paper_2109_07358_gb300 import ffs
+    from paper_2109_07358_gb300 import workloads as w
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    U = w.haar(16, 4, seed=1, complex_=False)
+    with pytest.raises(ffs.FFSError) as e:
+        ffs.Sampler(U, 0)
+    assert e.value.code == ffs.FFS_E_CUDA
+    x = np.zeros((2, 4), np.int32)
+    with pytest.raises(ffs.FFSError) as e:
+        ffs.ffs_sample_noalloc(U, ffs.FFS_F64, 16, 4, 2, 0, x)
+    assert e.value.code == ffs.FFS_E_CUDA
