@@ -7,13 +7,15 @@
   difference between the wells is 0 in the balanced stage and 2 in the imbalanced one,
   and where the highest orbital is split between the wells the left count is a Bernoulli
   variable whose error over M samples is sqrt(p (1 - p) / M), p being that orbital's
-  weight in the left well.
+  weight in the left well;
+* Eq. 1 is symmetric in the order of x: given the set, the N! orders are uniform;
+* Eq. 2 by exact enumeration at (L, N) = (8, 4).
 
 Expected values come from determinants written out here (numpy's det over every
 subset), not from the oracle's own set-probability helper.
 """
 from collections import Counter
-from itertools import combinations
+from itertools import combinations, permutations
 
 import numpy as np
 from scipy.stats import chisquare
@@ -100,3 +102,39 @@ def test_double_well_bernoulli_error():
     print(f"double well, Bernoulli case: mean left count {nl.mean():.4f} (exact 1.5), "
           f"deviation {dev / eps:.2f} eps, eps = {eps:.4f}")
     assert dev < 5 * eps
+
+
+def test_orders_are_uniform_given_the_set():
+    """Eq. 1 is symmetric in the order of x, so given the set every one of the N! orders
+    is equally likely; checked on the most frequent sets of a complex U by chi-squared."""
+    U = w.haar(6, 3, seed=31)
+    M = 9000
+    X = orc.sample(U, M, seed=13)
+    by_set = {}
+    for x in X:
+        t = tuple(int(v) for v in x)
+        by_set.setdefault(tuple(sorted(t)), Counter())[t] += 1
+    top = sorted(by_set, key=lambda s: -sum(by_set[s].values()))[:4]
+    for S in top:
+        c = by_set[S]
+        obs = np.array([c.get(o, 0) for o in permutations(S)], float)
+        assert obs.sum() >= 300
+        p = chisquare(obs).pvalue
+        print(f"set {S}: {int(obs.sum())} samples over 6 orders, chi-squared p = {p:.3f}")
+        assert p > 1e-3
+
+
+def test_exact_enumeration_L8_N4():
+    """Eq. 2 at (L, N) = (8, 4): the chain averaged over all 24 column orders equals
+    |det U_x|^2 / N! (determinant written out here) for every one of the 1680 ordered x."""
+    from math import factorial
+
+    U = w.haar(8, 4, seed=84)
+    perms = list(permutations(range(4)))
+    total = 0.0
+    for x in permutations(range(8), 4):
+        avg = np.mean([orc.chain_probability(U, list(m), list(x)) for m in perms])
+        want = abs(np.linalg.det(U[list(x), :])) ** 2 / factorial(4)
+        assert abs(avg - want) < 1e-13
+        total += avg
+    assert abs(total - 1.0) < 1e-12
