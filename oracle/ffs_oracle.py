@@ -46,7 +46,8 @@ What pins each part (none compares the oracle with itself):
   * inverse_cdf: hand-made edge cases (zero weights, boundaries, the largest uniform,
     the rounding fallback).
   * sample_one / chain_probability: Eq. 2 by exact enumeration (the average over all N!
-    column orders equals |det U_x|^2 / N! for every ordered x, real and complex); the
+    column orders equals |det U_x|^2 / N! for every ordered x, real and complex, up to
+    L = 8, N = 4); orders uniform given the set (chi-squared); the
     conditional of every step against its determinant definition; the prefix marginal
     (N-k)!/N! det K_XX of marginal sampling; per-step invariants (Z = |h|^2, zero weight
     on drawn sites, prod |s_k|^2 = |det U_x|^2); N = 1 (Born rule), N = L, U = [I; 0]
