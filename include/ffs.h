@@ -200,18 +200,22 @@ int ffs_query(ffs_handle h, int64_t* L, int64_t* N, int* dtype, unsigned* flags,
  * instead.  All working memory comes from one fixed array of FFS_NOALLOC_SCRATCH_BYTES
  * in device global memory that the library declares statically: every GPU that loads
  * the library holds that memory until the process exits.
- *   U          device pointer, row-major L x N, dtype FFS_F64 or FFS_C128 (U^dagger U = 1
- *              is assumed, not checked).
+ *   U          device (or managed) pointer, row-major L x N, dtype FFS_F64 or FFS_C128
+ *              (U^dagger U = 1 is assumed, not checked).  Host memory is FFS_E_ARG.
  *   L, N, B    1 <= N <= L, B >= 0 samples; sample b uses Philox sample index b.
  *   seed       Philox key, as in ffs_sample.
- *   out_x      device pointer, B x N int32, sites in draw order.
+ *   out_x      device (or managed) pointer, B x N int32, sites in draw order.  A sample
+ *              whose chain reaches a degenerate step (no site with a positive finite
+ *              weight, a non-finite or zero normaliser, or a vanishing pivot) has -1 from
+ *              that step to the end of its row: there is no status word, so -1 is how a
+ *              caller detects it.
  *   cuda_stream  cudaStream_t or NULL.
  * The samples equal those of ffs_sample_ex with FFS_RES_FP32 | FFS_STATE_FP64 |
  * FFS_TAIL_UNBLOCKED (the same arithmetic in the same order, fused into one kernel;
  * meant for small problems).
  * A size whose working set (about B (8 N^2 + 4 L + 8 N) bytes, twice the N^2 term for
- * complex U) does not fit the array is rejected with FFS_E_NOMEM and a message naming
- * the limit.  The first call on a device looks up the array's device address; make that
+ * complex U; at least 288 bytes per sample) does not fit the array is rejected with
+ * FFS_E_NOMEM and a message naming the limit.  The first call on a device looks up the array's device address; make that
  * first call before any stream capture.  Every call works in the same array, which
  * keeps the previous call's contents (the kernel clears what must start at zero), so
  * calls that overlap on the GPU, from different streams or threads, race.  Asynchronous;

@@ -18,6 +18,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "ffs_draw.cuh"
 #include "ffs_internal.cuh"
 
 namespace fermi {
@@ -31,8 +32,6 @@ void set_null_handle_error(const std::string& msg);  // defined in ffs_api.cu
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FFS_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-
-constexpr unsigned kFullMask = 0xffffffffu;
 
 struct NoAllocLayout {
   int64_t L, N, Kr, Kp, ldP, ldMask, B;
@@ -76,35 +75,23 @@ int64_t carve(NoAllocLayout& lay, unsigned char* base, int64_t L, int64_t N, int
   return off;
 }
 
-__device__ __forceinline__ double na_warp_sum(double v) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
-  return v;
-}
-__device__ __forceinline__ double na_warp_scan(double v, int lane) {
-  for (int o = 1; o < 32; o <<= 1) {
-    const double t = __shfl_up_sync(kFullMask, v, o);
-    if (lane >= o) v += t;
-  }
-  return v;
-}
-
 __device__ __forceinline__ void na_put(float* H, int col, double v) { H[col] = (float)v; }
 __device__ __forceinline__ void na_put(float* H, int col, cd v) {
   H[2 * col] = (float)v.re;
   H[2 * col + 1] = (float)v.im;
 }
 
-// One CTA (256 threads) runs the whole chain of sample blockIdx.x.
+// One CTA (256 threads) runs the whole chain of sample blockIdx.x.  A degenerate step
+// (no site with a positive finite weight, a non-finite or non-positive normaliser, or a
+// vanishing pivot) ends the sample's chain: that entry and the rest of its row are -1.
 template <typename S>
 __global__ void __launch_bounds__(256)
     noalloc_kernel(const void* __restrict__ U64, NoAllocLayout lay, uint64_t seed, int32_t* __restrict__ out_x) {
   constexpr bool CPLX = std::is_same<S, cd>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double s_wsum[8], s_wbase[8];
-  __shared__ int s_cand[8];
-  __shared__ int s_x;
-  __shared__ double s_Z;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ DrawShared dsh;
+  __shared__ int s_status;
+  const int tid = threadIdx.x;
   const int64_t b = blockIdx.x;
   const int64_t L = lay.L, N = lay.N, Kr = lay.Kr;
   int32_t* m = lay.m + b * N;
@@ -120,6 +107,7 @@ __global__ void __launch_bounds__(256)
   // The array keeps the previous call's contents: clear what must start at zero.
   for (int64_t i = tid; i < lay.ldMask; i += blockDim.x) mask[i] = 0u;
   for (int64_t i = tid; i < lay.Kp; i += blockDim.x) H[i] = 0.f;
+  if (tid == 0) s_status = 0;
   __syncthreads();
   if (tid == 0) {  // column order: Fisher-Yates from Philox stream 0
     for (int64_t i = 0; i < N; ++i) m[i] = (int32_t)i;
@@ -172,61 +160,13 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
 
-    // normaliser and inverse CDF (warp-shuffle block scan, fixed order)
-    const int64_t seg = ((L + 255) / 256) * 32;
-    const int64_t w0 = min(L, (int64_t)warp * seg), w1 = min(L, w0 + seg);
-    double ws = 0.0;
-    for (int64_t i = w0 + lane; i < w1; i += 32) ws += (double)prow[i];
-    ws = na_warp_sum(ws);
-    if (lane == 0) s_wsum[warp] = ws;
-    __syncthreads();
-    if (tid == 0) {
-      double acc = 0.0;
-      for (int w = 0; w < 8; ++w) {
-        s_wbase[w] = acc;
-        acc += s_wsum[w];
-      }
-      s_Z = acc;
-    }
-    __syncthreads();
-    const double Z = s_Z;
-    const double t = site_uniform(seed, (uint64_t)b, (int)k) * Z;
-    int cand = INT_MAX;
-    double carry = s_wbase[warp];
-    for (int64_t i0 = w0; i0 < w1; i0 += 32) {
-      const int64_t i = i0 + lane;
-      const double v = (i < w1) ? (double)prow[i] : 0.0;
-      const double inc = na_warp_scan(v, lane);
-      const unsigned hit = __ballot_sync(kFullMask, (i < w1) && v > 0.0 && (carry + inc > t));
-      if (hit) {
-        cand = (int)(i0 + __ffs(hit) - 1);
-        break;
-      }
-      carry += __shfl_sync(kFullMask, inc, 31);
-    }
-    if (lane == 0) s_cand[warp] = cand;
-    __syncthreads();
-    if (tid == 0) {
-      int xs = INT_MAX;
-      for (int w = 0; w < 8; ++w) xs = min(xs, s_cand[w]);
-      s_x = xs;
-    }
-    __syncthreads();
-    int x = s_x;
-    if (x == INT_MAX) {
-      int last = -1;
-      for (int64_t i = tid; i < L; i += blockDim.x)
-        if (prow[i] > 0.f) last = (int)i;
-      for (int o = 16; o; o >>= 1) last = max(last, __shfl_xor_sync(kFullMask, last, o));
-      if (lane == 0) s_cand[warp] = last;
-      __syncthreads();
-      if (tid == 0) {
-        int l = -1;
-        for (int w = 0; w < 8; ++w) l = max(l, s_cand[w]);
-        s_x = l < 0 ? 0 : l;
-      }
-      __syncthreads();
-      x = s_x;
+    // normaliser and inverse CDF: the draw of the batched forms (ffs_draw.cuh)
+    double Z = 0.0;
+    const int x = block_draw(prow, L, seed, (uint64_t)b, k, -1, &s_status, dsh, Z);
+    __syncthreads();  // s_status is final
+    if (s_status != 0 || !(Z > 0.0) || !isfinite(Z)) {
+      for (int64_t j = k + tid; j < N; j += blockDim.x) out_x[b * N + j] = -1;
+      return;  // uniform over the CTA
     }
     if (tid == 0) {
       out_x[b * N + k] = x;
@@ -247,6 +187,11 @@ __global__ void __launch_bounds__(256)
     for (int64_t j = tid; j < k; j += blockDim.x) wc[j] = W[j * N + k];
     __syncthreads();
     const S s = nv[k];
+    const double s2 = abs2(s);
+    if (!(s2 > 1e-300) || !isfinite(s2)) {  // the pivot vanished: x_{k+1} has no weight left
+      for (int64_t j = k + 1 + tid; j < N; j += blockDim.x) out_x[b * N + j] = -1;
+      return;  // uniform over the CTA
+    }
     for (int64_t c = k + 1 + tid; c < N; c += blockDim.x) {
       const S nc = nv[c] / s;
       for (int64_t j = 0; j < k; ++j) W[j * N + c] = fms(W[j * N + c], wc[j], nc);
@@ -259,6 +204,17 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
   }
+}
+
+// Device or managed memory (what the kernel may dereference); pageable or pinned host
+// memory is refused.  cudaPointerGetAttributes allocates nothing.
+bool na_is_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 std::mutex g_setup_mutex;
@@ -276,6 +232,15 @@ extern "C" int ffs_sample_noalloc(const void* U, int dtype, int64_t L, int64_t N
   if (!U || !out_x || B < 0 || N < 1 || L < N || (dtype != FFS_F64 && dtype != FFS_C128)) {
     set_null_handle_error("ffs_sample_noalloc: need device U (FFS_F64 or FFS_C128), 1 <= N <= L, B >= 0, out_x");
     return FFS_E_ARG;
+  }
+  // The smallest working set is 288 bytes per sample (L = N = 1); a larger B cannot fit,
+  // and refusing it here keeps the size arithmetic below from overflowing.
+  if (B > (int64_t)(FFS_NOALLOC_SCRATCH_BYTES / 288) || N > 4096 || L > ((int64_t)1 << 24)) {
+    set_null_handle_error("ffs_sample_noalloc: B = " + std::to_string((long long)B) + ", L = " +
+                          std::to_string((long long)L) + ", N = " + std::to_string((long long)N) +
+                          " cannot fit the fixed " + std::to_string((long long)FFS_NOALLOC_SCRATCH_BYTES) +
+                          "-byte array");
+    return FFS_E_NOMEM;
   }
   const bool cplx = dtype == FFS_C128;
   NoAllocLayout lay;
@@ -296,6 +261,10 @@ extern "C" int ffs_sample_noalloc(const void* U, int dtype, int64_t L, int64_t N
   if (e != cudaSuccess || dev < 0 || dev >= 64) {
     set_null_handle_error("ffs_sample_noalloc: no usable current device");
     return FFS_E_CUDA;
+  }
+  if (!na_is_device(U) || !na_is_device(out_x)) {
+    set_null_handle_error("ffs_sample_noalloc: U and out_x must be device (or managed) memory");
+    return FFS_E_ARG;
   }
   {
     // First call on a device: look up the array's device address (and allow the

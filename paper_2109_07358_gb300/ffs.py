@@ -161,7 +161,11 @@ def ffs_sample_metropolis(h, B: int, seed: int, first_sample_index: int, n_steps
 
 def ffs_sample_noalloc(U, dtype: int, L: int, N: int, B: int, seed: int, out_x, stream=None):
     """Sampling that allocates no device memory (fixed working array in the library);
-    for callers that cannot allocate.  U and out_x must be device memory."""
+    for callers that cannot allocate.  U and out_x must be device memory; a row of
+    out_x that holds -1 from some step on is a sample whose chain became degenerate."""
+    for name, t in (("U", U), ("out_x", out_x)):
+        if hasattr(t, "is_cuda") and not t.is_cuda:
+            raise TypeError(f"ffs_sample_noalloc: {name} must be a CUDA tensor")
     _check(lib().ffs_sample_noalloc(_ptr(U), dtype, L, N, B, seed, _ptr(out_x), _stream(stream)))
 
 

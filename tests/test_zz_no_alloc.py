@@ -73,3 +73,43 @@ def test_noalloc_rejects_sizes_beyond_the_array():
         ffs.ffs_sample_noalloc(U, ffs.dtype_of(U), 64, 32, 1 << 20, 0, out)
     assert e.value.code == ffs.FFS_E_NOMEM
     assert "fixed" in str(e.value)
+
+
+def test_noalloc_refuses_host_buffers():
+    """U and out_x must be device memory: the library checks the pointers itself and
+    returns FFS_E_ARG for host memory (called through the C ABI, past the binding)."""
+    import ctypes
+
+    U = torch.from_numpy(w.haar(40, 6, seed=2)).cuda()
+    host_out = np.zeros((4, 6), dtype=np.int32)
+    lib = ffs.lib()
+    rc = lib.ffs_sample_noalloc(ctypes.c_void_p(U.data_ptr()), ffs.FFS_F64, 40, 6, 4, 0,
+                                ctypes.c_void_p(host_out.ctypes.data), None)
+    assert rc == ffs.FFS_E_ARG
+    assert "device" in lib.ffs_last_error(None).decode()
+    host_U = np.ascontiguousarray(w.haar(40, 6, seed=2))
+    dev_out = torch.empty((4, 6), dtype=torch.int32, device="cuda")
+    rc = lib.ffs_sample_noalloc(ctypes.c_void_p(host_U.ctypes.data), ffs.FFS_F64, 40, 6, 4, 0,
+                                ctypes.c_void_p(dev_out.data_ptr()), None)
+    assert rc == ffs.FFS_E_ARG
+    with pytest.raises(TypeError):
+        ffs.ffs_sample_noalloc(U.cpu(), ffs.FFS_F64, 40, 6, 4, 0, dev_out)
+
+
+def test_noalloc_marks_degenerate_chains_with_minus_one():
+    """A zero column of U makes every weight vanish at the step whose column it is (the
+    normaliser is 0): that entry and the rest of the row are -1, the earlier entries are
+    distinct sites.  The step is known in advance from the sample's column order."""
+    L, N, B, seed, zero_col = 40, 6, 64, 3, 2
+    Un = w.haar(L, N, seed=4)
+    Un[:, zero_col] = 0.0
+    U = torch.from_numpy(np.ascontiguousarray(Un)).cuda()
+    out = torch.full((B, N), 7, dtype=torch.int32, device="cuda")
+    ffs.ffs_sample_noalloc(U, ffs.FFS_F64, L, N, B, seed, out)
+    torch.cuda.synchronize()
+    X = out.cpu().numpy()
+    for b in range(B):
+        kz = int(np.flatnonzero(o.permutation(seed, b, N) == zero_col)[0])
+        assert (X[b, kz:] == -1).all(), (b, kz, X[b])
+        pre = X[b, :kz]
+        assert ((pre >= 0) & (pre < L)).all() and len(set(pre.tolist())) == kz
