@@ -6,12 +6,18 @@ draw + state-update steps) over one batch of B samples of the workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ffs|reference]
 
-Default workload: 64 x 64 open square lattice with random U(1) hopping phases
-(L = 4096), the N = 1024 lowest orbitals (complex), B = 4096 samples, seed 0.
-Prints one JSON line (rank 0).  Under torchrun each rank samples its own index
-range (weak scaling, no collective on the data path).  Each timed step has its own
-CUDA events (their sum is the step time; p50/p99 per call come from them); a workload
-whose working set fits in L2 gets the cache flushed between steps, outside the events.
+Default workload: the largest configuration, a 1D open Anderson chain L = 16384 with
+on-site disorder U[-1, 1] (seed 0), the N = 2048 lowest orbitals (real), B = 8192
+samples, Philox seed 0.  Prints one JSON line (rank 0).  Under torchrun each rank
+samples its own index range (weak scaling, no collective on the data path).  Each
+timed step has its own CUDA events (their sum is the step time; p50/p99 per call come
+from them); a workload whose working set fits in L2 gets the cache flushed between
+steps, outside the events.  `roofline` is the residual (GEMM) phase against the
+tensor-core peak of its precision; `roofline_tail` is the state update's dominant
+kernel.  Further sections: the plain per-sample FP32 form, the CPU oracle, end to end
+through host buffers, the 64 x 64 lattice workload (and its IEEE FP64 state), per-call
+latency of the L = 64 chain over 200 calls, marginal sampling, the L-ensemble, the
+grouped form, the large-L variant, reweighting, batching and a serving-rate sweep.
 """
 from __future__ import annotations
 
@@ -135,33 +141,11 @@ def blocked_flops_per_sample(N, cplx, nb=32):
     return {"step": step * f, "panel_s": panel_s * f, "panel": panel * f, "top": top * f}
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
-# captured launches of one timed step) of the dominant kernel, from one ncu capture of
-# this workload, with the digest of the kernel sources it was taken on: once those
-# sources change the figure is stale and is reported as null.
-NCU_TRAFFIC = {
-    # 64x64 lattice, B = 4096, old rows on the tensor cores (the kernel does Y, S^-1 Y and
-    # writes Bot): 31 launches of one timed step, 429.3 GB in all
-    ("tail_panel_kernel", "lattice64x64_N1024_B4096", "bf16x3", "df64", True): (13.85e9, "d7f98975133177fa"),
-}
-KERNEL_SOURCES = ("ffs_tail.cu", "ffs_arith.cuh", "ffs_kernels.cuh", "ffs_draw.cuh", "ffs_internal.cuh")
-
-
-def kernel_source_digest():
-    import hashlib
-
-    h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2109_07358_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
-def measured_traffic(kernel, args):
-    rec = NCU_TRAFFIC.get((kernel, args.workload, args.chosen, args.state, bool(args.trailing_tc)))
-    if rec is None or rec[1] != kernel_source_digest():
-        return None
-    return rec[0]
+# Instruction counts behind the derived CUDA-core peaks of the double-float state kernels:
+# a real lazy multiply-add (lz_mac) is 13 FP32-pipe instructions for 2 flops; a complex
+# one by Karatsuba is three of them (39 instructions) for 8 flops.
+DF_INSTR_REAL, DF_INSTR_COMPLEX = 13, 39
+FP32_INSTR_PER_S = 152 * 128 * 2.07e9   # FP32 lanes x max clock (nominal)
 
 
 class ClockSampler:
@@ -213,30 +197,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ CPU oracle
-def _oracle_worker(args):
-    U, seed, lo, hi = args
-    from oracle import ffs_oracle as o
-
-    o._single_thread()
-    t = time.perf_counter()
-    for s in range(lo, hi):
-        o.sample_one(U, seed, s)
-    return time.perf_counter() - t
-
-
-def oracle_baseline(U, n_samples, seed=0, workers=None):
-    """Time the CPU oracle (as it stands) on n_samples of the workload, one
-    single-threaded worker process per core (spawn)."""
-    import multiprocessing as mp
-
-    workers = max(1, min(workers or os.cpu_count() or 1, n_samples))
+def oracle_baseline(U, n_samples, seed=0, workers=None, threads=1):
+    """Time the CPU oracle (as it stands) on n_samples of the workload: one
+    single-threaded worker process per core (threads = 1), or one process whose BLAS
+    calls use `threads` threads (large workloads, where one sample is tens of seconds on
+    one core).  Returns (samples/s, wall seconds, cores used)."""
+    if threads > 1:
+        workers, blas = 1, str(threads)
+    else:
+        workers, blas = max(1, min(workers or os.cpu_count() or 1, n_samples)), "1"
     bounds = np.linspace(0, n_samples, workers + 1).astype(int)
     jobs = [(U, seed, int(bounds[i]), int(bounds[i + 1])) for i in range(workers)]
     saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    for v in saved:  # children start with single-threaded BLAS (read at their numpy import)
-        os.environ[v] = "1"
+    for v in saved:  # children read these at their numpy import
+        os.environ[v] = blas
     try:
-        return _oracle_pool(jobs, workers, n_samples)
+        rate, wall, _ = _oracle_pool(jobs, workers, n_samples, threads)
+        return rate, wall, max(workers, threads)
     finally:
         for v, old in saved.items():
             if old is None:
@@ -245,20 +222,40 @@ def oracle_baseline(U, n_samples, seed=0, workers=None):
                 os.environ[v] = old
 
 
-def oracle_sample_size(U, B, target_s=10.0):
-    """Samples of the workload to time the oracle on: one probe of one sample per core,
-    then as many as take about target_s of wall time on the same cores, at most B."""
-    n0 = max(2, os.cpu_count() or 1)
-    rate, _, _ = oracle_baseline(U, n0)
-    return int(min(max(n0, rate * target_s), max(n0, B)))
+def oracle_plan(U, B, target_s=10.0):
+    """(samples, BLAS threads) for a bounded oracle timing of about target_s of wall time.
+    Small workloads: one single-threaded worker per core, sized from a probe of one sample
+    per core.  Large ones (L N^2, x4 complex, above 1e9 multiply-adds, tens of seconds per
+    sample on one core): one process with BLAS on every core, whole samples, at least one."""
+    L, N = U.shape
+    cores = os.cpu_count() or 1
+    if L * N * N * (4 if np.iscomplexobj(U) else 1) <= 1e9:
+        n0 = max(2, cores)
+        rate, _, _ = oracle_baseline(U, n0)
+        return int(min(max(n0, rate * target_s), max(n0, B))), 1
+    rate, _, _ = oracle_baseline(U, 1, threads=cores)
+    return int(min(B, max(1, round(rate * target_s)))), cores
 
 
-def _oracle_pool(jobs, workers, n_samples):
+def _oracle_worker(args):
+    U, seed, lo, hi, threads = args
+    from oracle import ffs_oracle as o
+
+    if threads == 1:
+        o._single_thread()
+    t = time.perf_counter()
+    for s in range(lo, hi):
+        o.sample_one(U, seed, s)
+    return time.perf_counter() - t
+
+
+def _oracle_pool(jobs, workers, n_samples, threads=1):
     import multiprocessing as mp
 
     U = jobs[0][0]
+    jobs = [j + (threads,) for j in jobs]
     with mp.get_context("spawn").Pool(workers) as pool:
-        pool.map(_oracle_worker, [(U[:8, :2].copy() / np.linalg.norm(U[:8, :2], axis=0), 0, 0, 1)] * workers)
+        pool.map(_oracle_worker, [(U[:8, :2].copy() / np.linalg.norm(U[:8, :2], axis=0), 0, 0, 1, threads)] * workers)
         t0 = time.perf_counter()
         pool.map(_oracle_worker, jobs)
         wall = time.perf_counter() - t0
@@ -270,13 +267,15 @@ def run_reference(args, spec, rank, world):
     if rank != 0:
         return 0
     U = make_U(spec)
-    n = args.ref_samples or oracle_sample_size(U, spec["B"])
+    n, threads = oracle_plan(U, spec["B"])
+    if args.ref_samples:
+        n = args.ref_samples
     for _ in range(args.warmup):
-        oracle_baseline(U, max(1, n // 4))
+        oracle_baseline(U, max(1, n // 4), threads=threads)
     rates = []
     walls = []
     for _ in range(args.steps):
-        r, wall, workers = oracle_baseline(U, n)
+        r, wall, workers = oracle_baseline(U, n, threads=threads)
         rates.append(r)
         walls.append(wall)
     v = float(np.median(rates))
@@ -288,7 +287,8 @@ def run_reference(args, spec, rank, world):
         "config": {"workload": args.workload, "desc": spec["desc"], "B_per_step": n,
                    "sample": f"{n} samples of the workload per step (indices 0..{n - 1})"},
         "cpu_baseline": {"value": v, "unit": "samples/s", "cores": workers, "kind": "oracle",
-                         "sample": f"{n} samples per step, one single-threaded worker per core"},
+                         "sample": f"{n} samples per step, " + ("one single-threaded worker per core" if threads == 1
+                                                                 else f"one process, BLAS on {threads} threads")},
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -485,11 +485,12 @@ def bench_metropolis(flags, stream, B=4096, reps=3):
 
 
 def bench_serving(args, flags):
-    """Poisson stream of projection-DPP requests (U = top-N left singular vectors of L
+    """Poisson streams of projection-DPP requests (U = top-N left singular vectors of L
     unit-norm Gaussian features of dimension D; L log-uniform [500, 20000], D in [64, 512],
-    N in [5, min(200, D)], 1-32 samples) into the continuous-batching engine."""
+    N in [5, min(200, D)], 1-32 samples) into the continuous-batching engine.  First the
+    saturated throughput (every request submitted at once), then Poisson arrivals at
+    fractions of it; latency is submission to completion (p50 / p99 / mean per rate)."""
     import numpy as np
-    import torch
 
     from paper_2109_07358_gb300 import ffs
     from paper_2109_07358_gb300 import workloads as w
@@ -497,47 +498,196 @@ def bench_serving(args, flags):
     sizes = w.serving_requests(args.requests, seed=0)
     Us = [w.lensemble_orbitals_torch(L, D, N, seed=1000 + i).cpu().numpy() for i, (L, D, N, _) in enumerate(sizes)]
     outs = [np.empty((s, N), dtype=np.int32) for (L, D, N, s) in sizes]
-    rng = np.random.default_rng(1)
-    gaps = rng.exponential(1.0 / args.rate, size=len(sizes))
-    srv = ffs.ffs_server_create(0, flags, 0)
-    ids = []
-    t0 = time.perf_counter()
-    t_next = t0
-    for i, (L, D, N, s) in enumerate(sizes):
-        t_next += gaps[i]
-        while time.perf_counter() < t_next:
-            time.sleep(0.0002)
-        ids.append(ffs.ffs_submit(srv, Us[i], ffs.FFS_F64, L, N, s, 7 + i, outs[i]))
-    lat = [ffs.ffs_wait(srv, rid, 600_000) for rid in ids]
-    wall = time.perf_counter() - t0
-    stats = ffs.ffs_server_stats(srv)
-    ffs.ffs_server_destroy(srv)
     samples = sum(s for (_, _, _, s) in sizes)
-    return {"workload": f"{len(sizes)} Poisson requests at {args.rate:g}/s, L log-uniform [500, 20000], "
-                        f"D uniform [64, 512], N uniform [5, min(200, D)], 1-32 samples",
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(np.mean(lat)), "samples_per_s": samples / wall, "requests": len(sizes),
-            "engine_iterations": stats["iterations"]}
+
+    def run(rate):
+        gaps = np.random.default_rng(1).exponential(1.0 / rate, size=len(sizes)) if rate else np.zeros(len(sizes))
+        srv = ffs.ffs_server_create(0, flags, 0)
+        ids = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for i, (L, D, N, s) in enumerate(sizes):
+            t_next += gaps[i]
+            while time.perf_counter() < t_next:
+                time.sleep(0.0002)
+            ids.append(ffs.ffs_submit(srv, Us[i], ffs.FFS_F64, L, N, s, 7 + i, outs[i]))
+        lat = [ffs.ffs_wait(srv, rid, 600_000) for rid in ids]
+        wall = time.perf_counter() - t0
+        st = ffs.ffs_server_stats(srv)
+        ffs.ffs_server_destroy(srv)
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(np.mean(lat)), "samples_per_s": samples / wall,
+                "requests_per_s": len(sizes) / wall, "engine_iterations": st["iterations"],
+                "peak_requests_per_iteration": st["peak_active"]}
+
+    run(0)  # warm-up: tile tuning of the size classes, allocator
+    sat = run(0)
+    sat_rps = sat["requests_per_s"]
+    sweep = []
+    for f in args.serving_fractions:
+        r = run(f * sat_rps)
+        r["fraction_of_saturated"] = f
+        r["offered_requests_per_s"] = f * sat_rps
+        sweep.append(r)
+    return {"workload": f"{len(sizes)} L-ensemble requests, L log-uniform [500, 20000], D uniform [64, 512], "
+                        f"N uniform [5, min(200, D)], 1-32 samples ({samples} samples)",
+            "saturated": sat, "sweep": sweep,
+            "latency": "submission to completion per request (ffs_wait), p50 / p99 over the requests"}
+
+
+def bench_latency_chain(flags, stream, calls=200):
+    """Per-call latency of the small plain workload (open chain L = 64, N = 8, B = 10^4,
+    seed 0): each call has its own CUDA events; its working set fits in L2, so a 516 MB
+    buffer is written between calls, outside the events."""
+    import torch
+
+    from paper_2109_07358_gb300 import ffs
+    from paper_2109_07358_gb300 import workloads as w
+
+    U = torch.from_numpy(w.chain_L64_N8()).cuda()
+    B = 10_000
+    S = ffs.Sampler(U, flags, stream=stream)
+    x = torch.empty((B, 8), dtype=torch.int32, device="cuda")
+    flush = torch.empty(4 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    for i in range(3):
+        ffs.ffs_sample_ex(S.h, B, 0, 0, 0, x, stream=stream)
+    S.sync()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+    with torch.cuda.stream(stream):
+        for i in range(calls):
+            flush.fill_(i)
+            evs[i][0].record(stream)
+            ffs.ffs_sample_ex(S.h, B, 0, 0, 0, x, stream=stream)
+            evs[i][1].record(stream)
+    S.sync()
+    ms = np.array([a.elapsed_time(b) for a, b in evs])
+    S.close()
+    return {"workload": "chain64_N8_B10000", "calls": calls, "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)), "samples_per_s": B / (float(np.median(ms)) / 1e3),
+            "l2": "516 MB written between calls, outside the events"}
 
 
 # ------------------------------------------------------------------------------ GPU path
+def run_timed(S, B, steps, warmup, rank, world, stream, x, local, flush_needed, n_steps=0):
+    """W warm-up calls, then K timed calls of B samples (each with its own CUDA events on
+    the handle's stream, per-phase profiling on, clocks sampled meanwhile)."""
+    import torch
+
+    from paper_2109_07358_gb300 import ffs
+    from paper_2109_07358_gb300.shard import step_offset
+
+    def step(i):
+        ffs.ffs_sample_ex(S.h, B, 0, step_offset(i, rank, world, B), n_steps, x, stream=stream)
+
+    for i in range(warmup):
+        step(i)
+    S.sync()
+    flush = torch.empty(4 * L2_BYTES // 4, dtype=torch.int32, device="cuda") if flush_needed else None
+    ffs.ffs_profile(S.h, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    return step, flush, evs
+
+
+def phase_report(prof, L, N, B, K, cplx, chosen, state, peaks, trailing_tc):
+    """Per-phase times and rates, the residual (GEMM) roofline against the tensor-core
+    peak of its precision, and the state update's dominant kernel against its peak."""
+    res_ms, res_n = prof["residual"]
+    tail_ms, tail_n = prof["tail"]
+    panel_ms, panel_n = prof["panel"]
+    pans_ms, pans_n = prof["panel_s"]
+    ptc_ms, ptc_n = prof["panel_tc"]
+    perm_ms, perm_n = prof["perm"]
+    res_flops = flops_per_sample(L, N, cplx) * B * K
+    issued = (2 * (2 * L) * (2 * N) * N if cplx else 2 * L * N * N) * B * K
+    bf = {k: v * B * K for k, v in blocked_flops_per_sample(N, cplx).items()}
+    mult = {"bf16x3": 3, "fp32": 1, "tf32": 1, "bf16": 1}[chosen]
+
+    def tfl(fl, ms):
+        return fl / (ms / 1e3) / 1e12 if ms else None
+
+    if chosen == "fp32":
+        res_peak, res_bound, res_src = NOMINAL_FP32_TFLOPS, "alu", "nominal FP32 rate (CUDA cores)"
+        tensor_peak = None
+    else:
+        tensor_peak = peaks["bf16_sus"] / (2 if chosen == "tf32" else 1)
+        res_peak, res_bound = tensor_peak / mult, "tensor"
+        res_src = (f"{peaks['source']} bf16_tflops_sustained {peaks['bf16_sus']}" +
+                   {"bf16x3": " / 3 (three BF16 products per term)", "tf32": " / 2 (TF32 rate)", "bf16": ""}[chosen])
+    ach = tfl(res_flops, res_ms)
+    roof = {"kernel": "residual_tc_kernel" if chosen != "fp32" else "residual_fp32_kernel", "phase": "residual (GEMM)",
+            "bound": res_bound, "achieved": ach, "peak": res_peak, "unit": "TFLOP/s",
+            "frac": ach / res_peak if ach else None,
+            "issued_achieved": tfl(issued * mult, res_ms) if tensor_peak else None,
+            "issued_frac": (tfl(issued * mult, res_ms) / tensor_peak) if tensor_peak and res_ms else None,
+            "traffic": None, "peak_source": res_src + " (measured; the kernel runs inside a long step)",
+            "algorithmic": "the paper's 2Lk flops per sample-step, L N (N+1) per sample" + (" x4 complex" if cplx else ""),
+            "per_launch": "algorithmic flops of all residual launches / their summed CUDA-event time"}
+    phases = {
+        "residual": {"kernel": roof["kernel"], "ms": res_ms / K, "launches_per_step": res_n / K,
+                     "algorithmic_tflops": ach, "issued_tflops": tfl(issued * mult, res_ms)},
+        "tail_step": {"kernel": "tail_step_kernel", "ms": tail_ms / K, "launches_per_step": tail_n / K,
+                      "algorithmic_tflops": tfl(bf["step"], tail_ms)},
+        "tail_panel_s": {"kernel": "tail_panel_s_kernel", "ms": pans_ms / K, "launches_per_step": pans_n / K,
+                         "algorithmic_tflops": tfl(bf["panel_s"], pans_ms)},
+        "tail_panel": {"kernel": "tail_panel_kernel", "ms": panel_ms / K, "launches_per_step": panel_n / K,
+                       "algorithmic_tflops": tfl(bf["panel"] - (bf["top"] if ptc_n else 0.0), panel_ms)},
+        "perm": {"kernel": "perm_init_kernel", "ms": perm_ms / K, "launches_per_step": perm_n / K},
+    }
+    if ptc_n:
+        phases["tail_panel_tc"] = {"kernel": "oz_top_kernel (+ slices, operand)", "ms": ptc_ms / K,
+                                   "launches_per_step": ptc_n / K, "algorithmic_tflops": tfl(bf["top"], ptc_ms)}
+    # the state update's largest CUDA-core kernel against the peak of its own arithmetic
+    if state == "df64":
+        instr = DF_INSTR_COMPLEX if cplx else DF_INSTR_REAL
+        st_peak = FP32_INSTR_PER_S / instr * (8 if cplx else 2) / 1e12
+        st_src = (f"derived: {FP32_INSTR_PER_S / 1e12:.1f} T FP32 instructions/s (152 SMs x 128 lanes x 2.07 GHz) / "
+                  f"{instr} instructions per {'complex (Karatsuba)' if cplx else 'real'} double-float multiply-add "
+                  f"x {8 if cplx else 2} flops")
+    elif state == "fp64":
+        st_peak, st_src = NOMINAL_FP64_TFLOPS, "nominal FP64 rate (1.25 TFLOP/s; 1.22 measured by an FMA loop)"
+    else:
+        st_peak, st_src = NOMINAL_FP32_TFLOPS, "nominal FP32 rate (152 SMs x 128 lanes x 2 x 2.07 GHz)"
+    fl_panel = bf["panel"] - (bf["top"] if ptc_n else 0.0)
+    tail_ach = tfl(fl_panel, panel_ms)
+    roof_tail = {"kernel": f"tail_panel_kernel ({state} state)", "bound": "alu", "achieved": tail_ach,
+                 "peak": st_peak, "unit": "TFLOP/s", "frac": tail_ach / st_peak if tail_ach else None,
+                 "traffic": None, "peak_source": st_src,
+                 "share_of_step": panel_ms / max(1e-9, res_ms + tail_ms + panel_ms + pans_ms + ptc_ms + perm_ms)}
+    launches = int(res_n + tail_n + panel_n + pans_n + ptc_n + perm_n) // K
+    return phases, roof, roof_tail, launches
+
+def section(out, name, fn):
+    """Run an optional section; a failure is recorded in the line instead of losing it."""
+    t0 = time.perf_counter()
+    try:
+        out[name] = fn()
+    except Exception as e:  # noqa: BLE001 - the headline must survive a failing extra section
+        out[name] = {"error": f"{type(e).__name__}: {e}"}
+    if isinstance(out[name], dict):
+        out[name]["section_wall_s"] = round(time.perf_counter() - t0, 1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ffs", choices=["ffs", "reference"])
-    ap.add_argument("--workload", default="lattice64x64_N1024_B4096", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="anderson_L16384_N2048_B8192", choices=list(WORKLOADS))
     ap.add_argument("--B", type=int, default=0, help="override samples per step")
     ap.add_argument("--chosen", default="bf16x3", choices=["bf16x3", "fp32", "tf32", "bf16"])
     ap.add_argument("--state", default="df64", choices=["df64", "fp64", "fp32"])
     ap.add_argument("--no-trailing-tc", dest="trailing_tc", action="store_false",
-                    help="keep the old rows' trailing update on the CUDA cores (default: tensor cores, BF16 "
-                         "slices of the double-float operands)")
+                    help="keep the old rows' trailing update on the CUDA cores (default: tensor cores for complex U)")
+    ap.add_argument("--plain-B", type=int, default=1024, help="samples of the timed plain-form call")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-samples", type=int, default=0)
+    ap.add_argument("--no-lattice", action="store_true", help="skip the 64x64 lattice section")
+    ap.add_argument("--no-fp64-state", action="store_true", help="skip the IEEE FP64 state section")
+    ap.add_argument("--no-latency", action="store_true", help="skip the per-call latency of the L = 64 chain")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-marginal", action="store_true")
     ap.add_argument("--marginal-steps", type=int, default=128)
@@ -548,7 +698,7 @@ def main():
     ap.add_argument("--no-grouped", action="store_true")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
-    ap.add_argument("--rate", type=float, default=300.0, help="serving arrivals per second")
+    ap.add_argument("--serving-fractions", type=float, nargs="*", default=[0.25, 0.5, 0.75, 0.9, 1.1])
     args = ap.parse_args()
     spec = dict(WORKLOADS[args.workload])
     if args.B:
@@ -587,30 +737,24 @@ def main():
     res_flag = {"bf16x3": ffs.FFS_RES_BF16X3, "fp32": ffs.FFS_RES_FP32, "tf32": ffs.FFS_RES_TF32,
                 "bf16": ffs.FFS_RES_BF16}[args.chosen]
     state_flag = {"df64": ffs.FFS_STATE_DF64, "fp64": ffs.FFS_STATE_FP64, "fp32": ffs.FFS_STATE_FP32}[args.state]
-    # the tensor-core trailing update pays for complex states; for real ones half of each
-    # slice row is zero padding and the direct update is faster (457 against 471 samples/s
-    # on the Anderson chain), so real U keeps the direct form
-    flags = res_flag | state_flag | (ffs.FFS_TRAILING_TC if args.trailing_tc and cplx and args.state == "df64" else 0)
-    flags_real = flags & ~ffs.FFS_TRAILING_TC  # the sections with real or mixed U
+
+    def flags_for(is_cplx):
+        # the tensor-core old-row update pays for complex states; for real ones half of each
+        # slice row is zero padding and the direct update is faster
+        tc = args.trailing_tc and is_cplx and args.state == "df64" and args.chosen != "fp32"
+        return res_flag | state_flag | (ffs.FFS_TRAILING_TC if tc else 0)
+
+    flags = flags_for(cplx)
+    flags_real = flags_for(False)  # the sections with real or mixed U
     stream = torch.cuda.Stream()
     S = ffs.Sampler(U, flags, stream=stream)
     x = torch.empty((B, N), dtype=torch.int32, device="cuda")
-    from paper_2109_07358_gb300.shard import step_offset
-
-    def step(i):
-        ffs.ffs_sample_ex(S.h, B, 0, step_offset(i, rank, world, B), 0, x, stream=stream)
-
-    for i in range(args.warmup):
-        step(i)
-    S.sync()
     # a working set that fits in L2 twice over is evicted between timed steps by writing a
     # buffer larger than L2, outside the per-step events; otherwise the steps run back to
     # back and each step's inputs are larger than L2 already
     ws = working_set_bytes(L, N, B, cplx, args.state)
-    flush = torch.empty(4 * L2_BYTES // 4, dtype=torch.int32, device="cuda") if ws < 2 * L2_BYTES else None
-    ffs.ffs_profile(S.h, True)
+    step, flush, evs = run_timed(S, B, args.steps, args.warmup, rank, world, stream, x, local, ws < 2 * L2_BYTES)
     barrier()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         torch.cuda.nvtx.range_push("timed")   # lets a profiler capture the timed steps only
         with torch.cuda.stream(stream):
@@ -627,169 +771,232 @@ def main():
     ms_total = float(step_ms.sum())
     prof = ffs.ffs_profile_read(S.h)
     ffs.ffs_profile(S.h, False)
+    del flush
     if dist is not None:
         t = torch.tensor([ms_total], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = float(t.item())
     ms_step = ms_total / args.steps
     value = world * B / (ms_step / 1e3)
-
-    # per-kernel time (CUDA events around every launch on the handle's stream) and roofline
-    res_ms, res_n = prof["residual"]
-    tail_ms, tail_n = prof["tail"]
-    panel_ms, panel_n = prof["panel"]
-    pans_ms, pans_n = prof["panel_s"]
-    ptc_ms, ptc_n = prof["panel_tc"]
-    perm_ms, perm_n = prof["perm"]
-    K = args.steps
-    res_flops = flops_per_sample(L, N, cplx) * B * K
-    issued = 2 * (2 * L) * (2 * N) * N * B * K if cplx else 2 * L * N * N * B * K
-    bf = {k: v * B * K for k, v in blocked_flops_per_sample(N, cplx).items()}
-    mult = {"bf16x3": 3, "fp32": 1, "tf32": 1, "bf16": 1}[args.chosen]
-    if args.chosen == "fp32":
-        res_peak, res_unit, res_bound = NOMINAL_FP32_TFLOPS, "TFLOP/s", "alu"
-    elif args.chosen == "tf32":
-        res_peak, res_unit, res_bound = peaks["bf16_sus"] / 2, "TFLOP/s", "tensor"
-    else:
-        res_peak, res_unit, res_bound = peaks["bf16_sus"] / mult, "TFLOP/s", "tensor"
-    # a double-float multiply-add takes about 12 FP32-pipe instructions (exact product of
-    # the high parts by FMA, cross terms, error-free sum), so its peak is FP32 / 12
-    st_peak, st_src = {"fp64": (NOMINAL_FP64_TFLOPS, "nominal FP64 rate (1.25 TFLOP/s)"),
-                       "fp32": (NOMINAL_FP32_TFLOPS, "nominal FP32 rate (152 SMs x 128 lanes x 2 x 2.07 GHz)"),
-                       "df64": (NOMINAL_FP32_TFLOPS / 12, "nominal FP32 rate / 12 (FP32-pipe instructions per "
-                                "double-float multiply-add)")}[args.state]
-
-    def tfl(fl, ms):
-        return fl / (ms / 1e3) / 1e12 if ms else None
-
-    phases = {
-        "residual": {"kernel": "residual_tc_kernel" if args.chosen != "fp32" else "residual_fp32_kernel",
-                     "ms": res_ms / K, "launches_per_step": res_n / K,
-                     "algorithmic_tflops": tfl(res_flops, res_ms), "issued_tflops": tfl(issued * mult, res_ms)},
-        "tail_step": {"kernel": "tail_step_kernel", "ms": tail_ms / K, "launches_per_step": tail_n / K,
-                      "algorithmic_tflops": tfl(bf["step"], tail_ms)},
-        "tail_panel_s": {"kernel": "tail_panel_s_kernel", "ms": pans_ms / K, "launches_per_step": pans_n / K,
-                         "algorithmic_tflops": tfl(bf["panel_s"], pans_ms)},
-        "tail_panel": {"kernel": "tail_panel_kernel", "ms": panel_ms / K, "launches_per_step": panel_n / K,
-                       "algorithmic_tflops": tfl(bf["panel"] - (bf["top"] if ptc_n else 0.0), panel_ms)},
-        "perm": {"kernel": "perm_init_kernel", "ms": perm_ms / K, "launches_per_step": perm_n / K},
-    }
-    if ptc_n:
-        phases["tail_panel_tc"] = {"kernel": "oz_top_kernel (+ slices, operand)", "ms": ptc_ms / K,
-                                   "launches_per_step": ptc_n / K, "algorithmic_tflops": tfl(bf["top"], ptc_ms)}
-    cand = {"residual": res_ms, "tail_step": tail_ms, "tail_panel_s": pans_ms, "tail_panel": panel_ms}
-    dominant = max(cand, key=cand.get)
-    if dominant == "residual":
-        ach = res_flops / (res_ms / 1e3) / 1e12
-        roof = {"kernel": phases["residual"]["kernel"], "bound": res_bound, "achieved": ach, "peak": res_peak,
-                "unit": res_unit, "frac": ach / res_peak, "traffic": None,
-                "peak_source": f"{peaks['source']} bf16 sustained / {mult}" if res_bound == "tensor"
-                else "nominal FP32 rate"}
-    else:
-        fl = {"tail_step": bf["step"], "tail_panel_s": bf["panel_s"],
-              "tail_panel": bf["panel"] - (bf["top"] if ptc_n else 0.0)}[dominant]
-        ach = fl / (cand[dominant] / 1e3) / 1e12
-        roof = {"kernel": f"{phases[dominant]['kernel']} ({args.state} state)", "bound": "alu", "achieved": ach,
-                "peak": st_peak, "unit": "TFLOP/s", "frac": ach / st_peak,
-                "traffic": measured_traffic(phases[dominant]["kernel"], args),
-                "peak_source": st_src,
-                "per_launch": "algorithmic flops of all launches / their summed CUDA-event time"}
-
-    prof_launches = int(res_n + tail_n + panel_n + pans_n + ptc_n + perm_n) // args.steps
+    phases, roof, roof_tail, launches = phase_report(prof, L, N, B, args.steps, cplx, args.chosen, args.state, peaks,
+                                                     bool(flags & ffs.FFS_TRAILING_TC))
     out = {
         "metric": "FFS samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64" if cplx else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.chosen == "fp32" else args.chosen[:4],
+        "dtype_detail": {"bf16x3": "residual on tensor cores in BF16 (hi/lo split, three products, FP32 "
+                                   "accumulation)", "bf16": "residual in BF16 (FP32 accumulation)",
+                         "tf32": "residual in TF32 (FP32 accumulation)", "fp32": "residual in FP32 on CUDA cores"}
+        [args.chosen] + f"; {args.state} state" + (" (pairs of FP32 numbers)" if args.state == "df64" else ""),
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": spec["desc"], "L": L, "N": N, "B": B,
                    "form": f"batched {args.chosen} residual + {args.state} state" +
                            (" + tensor-core trailing update" if flags & ffs.FFS_TRAILING_TC else ""),
                    "working_set_bytes": ws,
-                   "l2": "inputs larger than L2 (steps back to back)" if flush is None else
+                   "l2": "inputs larger than L2 (steps back to back)" if ws >= 2 * L2_BYTES else
                    "working set below L2: a 516 MB buffer is written between timed steps, outside their "
                    "CUDA events"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "calls": int(args.steps), "what": "one ffs_sample_ex call of B samples (CUDA events)"},
         "clocks": clk.summary(),
-        "gpu_launches": prof_launches,
+        "gpu_launches": launches,
         "roofline": roof,
+        "roofline_tail": roof_tail,
         "phases": phases,
     }
-
-    if not args.no_plain and rank == 0:
-        P = ffs.Sampler(U, ffs.FFS_FORM_PLAIN, stream=stream)
-        xp = torch.empty((B, N), dtype=torch.int32, device="cuda")
-        ffs.ffs_sample_ex(P.h, min(B, 64), 0, 0, 0, xp, stream=stream)
-        P.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ffs.ffs_sample_ex(P.h, B, 0, 0, 0, xp, stream=stream)
-        e1.record(stream)
-        P.sync()
-        pms = e0.elapsed_time(e1)
-        out["plain"] = {"value": B / (pms / 1e3), "unit": "samples/s", "ms_per_step": pms,
-                        "form": "plain per-sample FP32 (CUDA cores, FP32 state)",
-                        "chosen_over_plain": value / world / (B / (pms / 1e3))}
-        P.close()
-
-    if not args.no_cpu and rank == 0:
-        n = oracle_sample_size(U_np, B)
-        rate, wall, workers = oracle_baseline(U_np, n)
-        out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": workers, "kind": "oracle",
-                               "sample": f"{n} samples of the same workload (indices 0..{n - 1}), "
-                                         f"{wall:.1f} s wall"}
-
-    if not args.no_marginal and rank == 0:
-        # marginal sampling: the first n of the N positions (the chain stopped after n steps)
-        nm = min(args.marginal_steps, N)
-        xm = torch.empty((B, nm), dtype=torch.int32, device="cuda")
-        ffs.ffs_sample_ex(S.h, B, 0, 0, nm, xm, stream=stream)
-        S.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ffs.ffs_sample_ex(S.h, B, 0, 0, nm, xm, stream=stream)
-        e1.record(stream)
-        S.sync()
-        mms = e0.elapsed_time(e1)
-        out["marginal"] = {"n_steps": nm, "samples_per_s": B / (mms / 1e3), "ms_per_batch": mms,
-                           "full_chain_ms_per_batch": ms_step}
-    if not args.no_reweight and rank == 0:
-        out["reweight"] = bench_reweight(x, spec, stream)
-    S.close()
-    if not args.no_e2e:
-        # End to end through the C ABI with host buffers: U uploaded from pinned host
-        # memory (ffs_create_ex), samples read back into pinned host memory.  Runs after
-        # the device-timed handle is released, so that both see the same free memory.
-        U_host = torch.from_numpy(U_np).pin_memory()
-        x_host = torch.empty((B, N), dtype=torch.int32).pin_memory()
-        times = []
-        for i in range(args.steps + 1):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            h = ffs.ffs_create_ex(U_host, ffs.dtype_of(U_host), L, N, N, flags, stream)
-            ffs.ffs_sample_ex(h, B, 0, step_offset(i, rank, world, B), 0, x_host, stream=stream)
-            ffs.ffs_destroy(h)
-            times.append(time.perf_counter() - t0)
-        e2e_s = float(np.median(times[1:]))
-        out["e2e"] = {"value": world * B / e2e_s, "unit": "samples/s",
-                      "h2d_bytes_per_step": int(U_host.numel() * U_host.element_size()),
-                      "d2h_bytes_per_step": int(x_host.numel() * 4)}
-
-    if not args.no_lensemble and rank == 0:
-        out["lensemble"] = bench_lensemble(flags_real, stream)
-    if not args.no_grouped and rank == 0:
-        out["grouped"] = bench_grouped(U, flags, B, L, N, cplx, peaks, args, stream)
-    if not args.no_metropolis and rank == 0:
-        out["metropolis"] = bench_metropolis(flags_real, stream)
-    if not args.no_batching and rank == 0:
-        out["batching"] = bench_batching(args, flags, stream)
-    if not args.no_serving and rank == 0:
-        out["serving"] = bench_serving(args, flags_real)
+    main_sections(args, out, ffs, torch, S, U, U_np, spec, flags, flags_real, stream, x, B, L, N, cplx, peaks,
+                  ms_step, rank, world)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def main_sections(args, out, ffs, torch, S, U, U_np, spec, flags, flags_real, stream, x, B, L, N, cplx, peaks,
+                  ms_step, rank, world):
+    """The sections after the headline (rank 0 only, except the end-to-end line)."""
+    from paper_2109_07358_gb300.shard import step_offset
+
+    def timed_call(h, n, seed, xo, n_steps=0):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ffs.ffs_sample_ex(h, n, seed, 0, n_steps, xo, stream=stream)
+        e1.record(stream)
+        ffs.ffs_sync(h)
+        return e0.elapsed_time(e1)
+
+    if not args.no_plain and rank == 0:
+        def plain():
+            nb = min(B, args.plain_B)
+            P = ffs.Sampler(U, ffs.FFS_FORM_PLAIN, stream=stream)
+            xp = torch.empty((nb, N), dtype=torch.int32, device="cuda")
+            ffs.ffs_sample_ex(P.h, min(nb, 64), 0, 0, 0, xp, stream=stream)
+            P.sync()
+            pms = timed_call(P.h, nb, 0, xp)
+            P.close()
+            return {"value": nb / (pms / 1e3), "unit": "samples/s", "ms_per_call": pms, "B": nb,
+                    "form": "plain per-sample FP32 (CUDA cores, FP32 state)",
+                    "chosen_over_plain": out["value"] / world / (nb / (pms / 1e3)),
+                    "note": f"samples 0..{nb - 1} of the same workload (the plain form's rate does not grow with B "
+                            "once the GPU is full)"}
+        section(out, "plain", plain)
+
+    if not args.no_cpu and rank == 0:
+        def cpu():
+            n, threads = oracle_plan(U_np, B)
+            rate, wall, workers = oracle_baseline(U_np, n, threads=threads)
+            return {"value": rate, "unit": "samples/s", "cores": workers, "kind": "oracle",
+                    "sample": f"{n} samples of the same workload (indices 0..{n - 1}), {wall:.1f} s wall, "
+                              + ("one single-threaded worker per core" if threads == 1 else
+                                 f"one process, BLAS on {workers} threads")}
+        section(out, "cpu_baseline", cpu)
+
+    if not args.no_marginal and rank == 0:
+        def marginal():
+            nm = min(args.marginal_steps, N)
+            xm = torch.empty((B, nm), dtype=torch.int32, device="cuda")
+            ffs.ffs_sample_ex(S.h, B, 0, 0, nm, xm, stream=stream)
+            S.sync()
+            mms = timed_call(S.h, B, 0, xm, nm)
+            return {"n_steps": nm, "samples_per_s": B / (mms / 1e3), "ms_per_batch": mms,
+                    "full_chain_ms_per_batch": ms_step}
+        section(out, "marginal", marginal)
+    if not args.no_reweight and rank == 0:
+        section(out, "reweight", lambda: bench_reweight(x, spec, stream))
+    S.close()
+    if not args.no_e2e:
+        def e2e():
+            # End to end through the C ABI with host buffers: U uploaded from pinned host
+            # memory (ffs_create_ex), samples read back into pinned host memory.  Runs after
+            # the device-timed handle is released, so that both see the same free memory.
+            U_host = torch.from_numpy(U_np).pin_memory()
+            x_host = torch.empty((B, N), dtype=torch.int32).pin_memory()
+            times = []
+            for i in range(args.e2e_steps + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h = ffs.ffs_create_ex(U_host, ffs.dtype_of(U_host), L, N, N, flags, stream)
+                ffs.ffs_sample_ex(h, B, 0, step_offset(i, rank, world, B), 0, x_host, stream=stream)
+                ffs.ffs_destroy(h)
+                times.append(time.perf_counter() - t0)
+            e2e_s = float(np.median(times[1:]))
+            return {"value": world * B / e2e_s, "unit": "samples/s",
+                    "h2d_bytes_per_step": int(U_host.numel() * U_host.element_size()),
+                    "d2h_bytes_per_step": int(x_host.numel() * 4), "steps": args.e2e_steps,
+                    "what": "host wall clock of ffs_create_ex (U from pinned host memory) + ffs_sample_ex into "
+                            "pinned host memory + ffs_destroy, median of the timed steps after one warm-up"}
+        section(out, "e2e", e2e)
+    if rank != 0:
+        return
+    if not args.no_latency:
+        section(out, "latency_chain64", lambda: bench_latency_chain(flags_for_chain(ffs, args), stream))
+    if not args.no_lattice and args.workload != "lattice64x64_N1024_B4096":
+        section(out, "lattice", lambda: bench_lattice(args, ffs, torch, stream, peaks))
+    if not args.no_fp64_state:
+        section(out, "fp64_state", lambda: bench_fp64_state(args, ffs, torch, stream))
+    if not args.no_lensemble:
+        section(out, "lensemble", lambda: bench_lensemble(flags_real, stream))
+    if not args.no_grouped:
+        section(out, "grouped", lambda: bench_grouped_lattice(args, ffs, torch, stream, peaks))
+    if not args.no_metropolis:
+        section(out, "metropolis", lambda: bench_metropolis(flags_real, stream))
+    if not args.no_batching:
+        section(out, "batching", lambda: bench_batching(args, res_and_state(ffs, args) |
+                                                        (ffs.FFS_TRAILING_TC if args.trailing_tc and
+                                                         args.state == "df64" and args.chosen != "fp32" else 0),
+                                                        stream))
+    if not args.no_serving:
+        section(out, "serving", lambda: bench_serving(args, flags_real))
+
+
+def res_and_state(ffs, args):
+    return ({"bf16x3": ffs.FFS_RES_BF16X3, "fp32": ffs.FFS_RES_FP32, "tf32": ffs.FFS_RES_TF32,
+             "bf16": ffs.FFS_RES_BF16}[args.chosen] |
+            {"df64": ffs.FFS_STATE_DF64, "fp64": ffs.FFS_STATE_FP64, "fp32": ffs.FFS_STATE_FP32}[args.state])
+
+
+def flags_for_chain(ffs, args):
+    return res_and_state(ffs, args)
+
+
+def lattice_flags(ffs, args, state=None):
+    st = state or args.state
+    tc = args.trailing_tc and st == "df64" and args.chosen != "fp32"
+    return ({"bf16x3": ffs.FFS_RES_BF16X3, "fp32": ffs.FFS_RES_FP32, "tf32": ffs.FFS_RES_TF32,
+             "bf16": ffs.FFS_RES_BF16}[args.chosen] |
+            {"df64": ffs.FFS_STATE_DF64, "fp64": ffs.FFS_STATE_FP64, "fp32": ffs.FFS_STATE_FP32}[st] |
+            (ffs.FFS_TRAILING_TC if tc else 0))
+
+
+_LATTICE = {}
+
+
+def lattice_U(torch):
+    if "U" not in _LATTICE:
+        from paper_2109_07358_gb300 import workloads as w
+
+        _LATTICE["np"] = w.lattice_64x64_N1024(0)
+        _LATTICE["U"] = torch.from_numpy(_LATTICE["np"]).cuda()
+    return _LATTICE["U"]
+
+
+def bench_lattice(args, ffs, torch, stream, peaks, steps=3):
+    """The 64 x 64 random-phase lattice (L = 4096, N = 1024, complex, B = 4096) in the
+    chosen form: one warm-up and `steps` timed calls with per-phase profiling."""
+    U = lattice_U(torch)
+    L, N, B = 4096, 1024, 4096
+    S = ffs.Sampler(U, lattice_flags(ffs, args), stream=stream)
+    x = torch.empty((B, N), dtype=torch.int32, device="cuda")
+    ffs.ffs_sample_ex(S.h, B, 0, 0, 0, x, stream=stream)
+    S.sync()
+    ffs.ffs_profile(S.h, True)
+    ms = []
+    for i in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ffs.ffs_sample_ex(S.h, B, 0, (1 + i) * B, 0, x, stream=stream)
+        e1.record(stream)
+        S.sync()
+        ms.append(e0.elapsed_time(e1))
+    prof = ffs.ffs_profile_read(S.h)
+    S.close()
+    phases, roof, roof_tail, launches = phase_report(prof, L, N, B, steps, True, args.chosen, args.state, peaks,
+                                                     args.trailing_tc)
+    m = float(np.mean(ms))
+    return {"workload": "lattice64x64_N1024_B4096", "samples_per_s": B / (m / 1e3), "ms_per_step": m,
+            "steps": steps, "roofline": roof, "roofline_tail": roof_tail, "phases": phases}
+
+
+def bench_fp64_state(args, ffs, torch, stream):
+    """The IEEE FP64 state against the chosen double-float state on the 64 x 64 lattice
+    (B = 4096, one timed call each after a 128-sample warm-up): the price of IEEE FP64 on
+    GB300's FP64 pipes."""
+    U = lattice_U(torch)
+    B, N = 4096, 1024
+    x = torch.empty((B, N), dtype=torch.int32, device="cuda")
+    res = {}
+    for st in ("fp64", "df64"):
+        S = ffs.Sampler(U, lattice_flags(ffs, args, st), stream=stream)
+        ffs.ffs_sample_ex(S.h, 128, 0, 0, 0, x[:128], stream=stream)
+        S.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ffs.ffs_sample_ex(S.h, B, 0, 0, 0, x, stream=stream)
+        e1.record(stream)
+        S.sync()
+        S.close()
+        ms = e0.elapsed_time(e1)
+        res[st] = {"samples_per_s": B / (ms / 1e3), "ms_per_call": ms}
+    res["workload"] = "lattice64x64_N1024_B4096"
+    res["df64_over_fp64"] = res["df64"]["samples_per_s"] / res["fp64"]["samples_per_s"]
+    return res
+
+
+def bench_grouped_lattice(args, ffs, torch, stream, peaks):
+    """The opt-in grouped form on the 64 x 64 lattice (one call after a warm-up)."""
+    U = lattice_U(torch)
+    return bench_grouped(U, lattice_flags(ffs, args), 4096, 4096, 1024, True, peaks, args, stream)
 
 
 if __name__ == "__main__":

@@ -315,7 +315,12 @@ int ffs_server_create(size_t hbm_budget, unsigned flags, int max_active, void* c
 int ffs_submit(ffs_server* s, const void* U, int dtype, int64_t L, int64_t N, int64_t n_samples, uint64_t seed,
                int32_t* out_x, uint64_t* req_id);
 int ffs_wait(ffs_server* s, uint64_t req_id, int timeout_ms, double* latency_ms);
-int ffs_server_stats(ffs_server* s, int64_t* pending, int64_t* active, int64_t* iterations, size_t* bytes_in_use);
+/* ffs_server_stats - queued and active requests, engine iterations so far, device bytes
+ * held for requests, and peak_active: the most requests one engine iteration advanced
+ * (requests advanced together share every launch of that iteration).  Any pointer may be
+ * NULL. */
+int ffs_server_stats(ffs_server* s, int64_t* pending, int64_t* active, int64_t* iterations, size_t* bytes_in_use,
+                     int64_t* peak_active);
 void ffs_server_destroy(ffs_server* s);
 
 /*
@@ -360,6 +365,22 @@ typedef struct {
 int ffs_jastrow_estimate(const int32_t* x, int64_t B, int64_t n_occ, int64_t n_orb, const ffs_csr* v,
                          const double* o, const ffs_csr* q, double* out_logj2, double* out_obs, double* result,
                          void* cuda_stream);
+
+/*
+ * ffs_debug_inject - failure-path testing.  Arms a one-shot fault for the next
+ * tensor-core residual launch of h (the paper has no counterpart: this exercises the
+ * library's bounded waits).  FFS_FAULT_SKIP_ARRIVAL: the TMA producer of that launch's
+ * first CTA skips its first pipeline stage (no arrival, no copy) and every wait of the
+ * launch gives up after 4096 polls instead of about 4 million, so the MMA issuer's wait
+ * runs out, the launch records FFS_E_TIMEOUT in the status word (ffs_sync returns it)
+ * and every role of the CTA leaves without a copy in flight and with its tensor memory
+ * freed.  The samples of that call are invalid; the handle stays usable and its next
+ * call samples normally.  Nothing faults, traps or hangs the GPU.  FFS_FAULT_NONE
+ * disarms.  FFS_E_UNSUPPORTED for a handle without a tensor-core residual.
+ */
+#define FFS_FAULT_NONE 0
+#define FFS_FAULT_SKIP_ARRIVAL 1
+int ffs_debug_inject(ffs_handle h, int fault);
 
 /* Phases reported by ffs_profile_read. */
 #define FFS_PHASE_PERM 0      /* column orders m and the step-0 operand              */

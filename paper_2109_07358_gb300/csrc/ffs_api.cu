@@ -793,6 +793,17 @@ int ffs_profile(ffs_handle h, int enable) {
   return FFS_OK;
 }
 
+int ffs_debug_inject(ffs_handle h, int fault) {
+  if (!h) return fail(nullptr, FFS_E_ARG, "ffs_debug_inject: NULL handle");
+  if (fault != FFS_FAULT_NONE && fault != FFS_FAULT_SKIP_ARRIVAL)
+    return fail(h, FFS_E_ARG, "ffs_debug_inject: unknown fault");
+  const int op = op_mode_of(h->flags);
+  if (fault != FFS_FAULT_NONE && (op == kOpNone || op == kOpF32))
+    return fail(h, FFS_E_UNSUPPORTED, "ffs_debug_inject: the handle has no tensor-core residual");
+  h->debug_fault = fault;
+  return FFS_OK;
+}
+
 int ffs_profile_read(ffs_handle h, double* ms, int64_t* launches, int n) {
   if (!h) return fail(nullptr, FFS_E_ARG, "ffs_profile_read: NULL handle");
   if (n < 0 || n > FFS_NUM_PHASES) return fail(h, FFS_E_ARG, "ffs_profile_read: bad n");

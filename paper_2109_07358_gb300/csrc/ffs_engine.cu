@@ -84,6 +84,8 @@ void fill_inst(GroupInst& g, ffs_ctx* c, int64_t B, uint64_t seed, uint64_t firs
   p.P = c->P;
   p.mask = c->mask;
   p.status = c->status;
+  p.spin = TcArgs{}.spin;  // the record was zeroed above: restore the wait limit
+  p.fault = 0;
   g.bn = c->res_bn ? c->res_bn : 256;
   g.n_jtiles = c->Lrp / g.bn;
   g.n_btiles = (B + 127) / 128;
@@ -334,6 +336,7 @@ struct ffs_server {
   size_t d_ent_cap = 0;
   std::atomic<int64_t> n_active{0};
   std::atomic<uint64_t> iterations{0};
+  std::atomic<int64_t> peak_active{0};  // most requests advanced by one engine iteration
 };
 
 namespace fermi {
@@ -424,6 +427,7 @@ void engine_loop(ffs_server* s) {
 
     // One iteration: every active request advances by one step, per real/complex group.
     const unsigned fl = s->flags;
+    int64_t advanced = 0;
     for (int g = 0; g < 2; ++g) {
       const bool cplx = g == 1;
       inst.clear();
@@ -498,8 +502,10 @@ void engine_loop(ffs_server* s) {
         r->started = true;
         r->k += 1;
       }
+      advanced += (int64_t)members.size();
     }
     ++s->iterations;
+    if (advanced > s->peak_active.load()) s->peak_active.store(advanced);
     (void)fl;
     // Completed requests: leave the active set first (a waiter may free a finished
     // request at once), then check the device status, copy the samples out, release.
@@ -615,9 +621,11 @@ int ffs_wait(ffs_server* s, uint64_t req_id, int timeout_ms, double* latency_ms)
   return status;
 }
 
-int ffs_server_stats(ffs_server* s, int64_t* pending, int64_t* active, int64_t* iterations, size_t* bytes_in_use) {
+int ffs_server_stats(ffs_server* s, int64_t* pending, int64_t* active, int64_t* iterations, size_t* bytes_in_use,
+                     int64_t* peak_active) {
   if (!s) return FFS_E_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
+  if (peak_active) *peak_active = s->peak_active.load();
   if (pending) *pending = (int64_t)s->pending.size();
   if (active) *active = s->n_active.load();
   if (iterations) *iterations = (int64_t)s->iterations.load();

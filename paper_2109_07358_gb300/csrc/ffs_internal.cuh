@@ -220,6 +220,7 @@ struct ffs_ctx {
   int64_t tmUg_groups = 0;
   int* status = nullptr;         // device status word
   int* status_host = nullptr;    // pinned mirror
+  int debug_fault = 0;           // FFS_FAULT_*: armed by ffs_debug_inject for the next launch
 
   // Optional per-phase timing with CUDA events on the launching stream.
   bool prof = false;

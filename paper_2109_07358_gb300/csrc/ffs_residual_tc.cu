@@ -106,14 +106,21 @@ __device__ __forceinline__ void residual_body(const CUtensorMap* tmA0p, const CU
       prefetch_tmap(&tmB1);
     }
     int issued = 0;
+    // failure-path test: the first CTA skips stage 0 (no arrival, no copy), so the MMA
+    // warp's wait for it runs out
+    const bool skip0 = p.fault && b0 == 0 && j0 == 0;
     const int32_t jg = j0 + (b0 / 128) * p.grp_rows;  // row of Ue (or of the sample group's copy)
     for (int kb = 0; kb < nK; ++kb) {
       const int s = kb % STAGES;
       const uint32_t round = kb / STAGES;
-      if (kb >= STAGES && !mbar_wait(empty(s), (round - 1) & 1, abort_flag)) {
+      if (kb >= STAGES && !mbar_wait_lim(empty(s), (round - 1) & 1, abort_flag, p.spin)) {
         *abort_flag = 1;
         set_status(p.status, FFS_E_TIMEOUT);
         break;
+      }
+      if (skip0 && kb == 0) {
+        ++issued;
+        continue;
       }
       const uint32_t st = sbase + s * C::STAGE_BYTES;
       mbar_arrive_expect_tx(full(s), C::STAGE_BYTES);
@@ -124,15 +131,16 @@ __device__ __forceinline__ void residual_body(const CUtensorMap* tmA0p, const CU
       if (C::NB == 2) tma_load_2d(st + C::NA * C::A_BYTES + C::B_BYTES, &tmB1, full(s), x, jg);
       ++issued;
     }
-    // Never leave with copies in flight: wait (bounded) for the last loads to land.
+    // Never leave with copies in flight: wait (bounded, even after an abort) for the last
+    // loads to land.
     for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-      mbar_wait(full(kb % STAGES), (kb / STAGES) & 1, abort_flag);
+      if (!(skip0 && kb == 0)) mbar_drain(full(kb % STAGES), (kb / STAGES) & 1, p.spin);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     for (int kb = 0; kb < nK; ++kb) {
       const int s = kb % STAGES;
       const uint32_t round = kb / STAGES;
-      if (!mbar_wait(full(s), round & 1, abort_flag)) {
+      if (!mbar_wait_lim(full(s), round & 1, abort_flag, p.spin)) {
         *abort_flag = 1;
         set_status(p.status, FFS_E_TIMEOUT);
         break;
@@ -162,7 +170,7 @@ __device__ __forceinline__ void residual_body(const CUtensorMap* tmA0p, const CU
     mma_commit(accum);
   } else if (warp >= 2) {
     // ---- epilogue: weights of 128 samples x BN embedding columns
-    const bool ok = mbar_wait(accum, 0, abort_flag);
+    const bool ok = mbar_wait_lim(accum, 0, abort_flag, p.spin);
     tc_fence_after();
     const int q = warp & 3;
     const int row = 32 * q + lane;
@@ -355,6 +363,11 @@ static cudaError_t launch_cfg(ffs_ctx* c, const StepArgs& a, cudaStream_t s) {
   p.P = a.P;
   p.mask = a.mask;
   p.status = a.status;
+  if (c->debug_fault == FFS_FAULT_SKIP_ARRIVAL) {  // one-shot, armed by ffs_debug_inject
+    p.fault = 1;
+    p.spin = 1u << 12;
+    c->debug_fault = FFS_FAULT_NONE;
+  }
   dim3 grid((unsigned)(c->Lrp / BN), (unsigned)((a.bw + 127) / 128));
   const CUtensorMap* tu = a.grouped ? c->tmUg : c->tmU;
   residual_tc_kernel<BN, STAGES, KIND><<<grid, 192, Cf::SMEM, s>>>(c->tmH[0], c->tmH[1], tu[0], tu[1], p);

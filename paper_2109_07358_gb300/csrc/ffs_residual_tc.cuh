@@ -14,6 +14,8 @@ struct TcArgs {
   float* P;
   const uint32_t* mask;
   int* status;
+  uint32_t spin = 1u << 22;  // polls before a wait gives up (FFS_E_TIMEOUT)
+  int fault = 0;             // failure-path test: the first CTA's producer skips stage 0
 };
 
 // P[b, y] = |sum_c H[b, c] Ue[j, c]|^2 on tcgen05 tensor cores (operand encoding op).

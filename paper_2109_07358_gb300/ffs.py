@@ -38,6 +38,7 @@ FFS_GROUP_SIZE = 128
 FFS_NO_ORTHO_CHECK = 0x1000
 FFS_TAIL_UNBLOCKED = 0x2000
 FFS_TRAILING_TC = 0x4000
+FFS_FAULT_NONE, FFS_FAULT_SKIP_ARRIVAL = 0, 1
 
 _lib = None
 
@@ -80,10 +81,11 @@ def lib() -> ctypes.CDLL:
         L.ffs_submit.argtypes = [vp, vp, i32, i64, i64, i64, u64, vp, ctypes.POINTER(u64)]
         L.ffs_wait.argtypes = [vp, u64, i32, ctypes.POINTER(ctypes.c_double)]
         L.ffs_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
-                                       ctypes.POINTER(ctypes.c_size_t)]
+                                       ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i64)]
         L.ffs_server_destroy.argtypes = [vp]
         L.ffs_server_destroy.restype = None
         L.ffs_profile.argtypes = [vp, i32]
+        L.ffs_debug_inject.argtypes = [vp, i32]
         L.ffs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]
         L.ffs_sample_metropolis.argtypes = [vp, i64, u64, u64, i64, i64, vp, vp, vp]
         L.ffs_sample_lensemble.argtypes = [vp, vp, i64, u64, u64, vp, vp, vp, vp, vp, vp, vp]
@@ -92,7 +94,7 @@ def lib() -> ctypes.CDLL:
         for name in ("ffs_create", "ffs_create_ex", "ffs_sample", "ffs_sample_ex", "ffs_sync", "ffs_query",
                      "ffs_profile", "ffs_profile_read", "ffs_sample_noalloc", "ffs_sample_batched",
                      "ffs_server_create", "ffs_submit", "ffs_wait", "ffs_server_stats", "ffs_jastrow_estimate",
-                     "ffs_sample_lensemble", "ffs_sample_metropolis"):
+                     "ffs_sample_lensemble", "ffs_sample_metropolis", "ffs_debug_inject"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -199,13 +201,20 @@ def ffs_wait(server, req_id: int, timeout_ms: int = -1) -> float:
 
 
 def ffs_server_stats(server):
-    p, a, it, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
-    _check(lib().ffs_server_stats(server, ctypes.byref(p), ctypes.byref(a), ctypes.byref(it), ctypes.byref(b)))
-    return {"pending": p.value, "active": a.value, "iterations": it.value, "bytes_in_use": b.value}
+    p, a, it, b, pk = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t(), ctypes.c_int64()
+    _check(lib().ffs_server_stats(server, ctypes.byref(p), ctypes.byref(a), ctypes.byref(it), ctypes.byref(b),
+                                  ctypes.byref(pk)))
+    return {"pending": p.value, "active": a.value, "iterations": it.value, "bytes_in_use": b.value,
+            "peak_active": pk.value}
 
 
 def ffs_server_destroy(server):
     lib().ffs_server_destroy(server)
+
+
+def ffs_debug_inject(h, fault: int):
+    """Failure-path testing: arm a one-shot fault for the next tensor-core residual launch."""
+    _check(lib().ffs_debug_inject(h, fault), h)
 
 
 def ffs_sync(h):

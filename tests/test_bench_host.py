@@ -67,3 +67,20 @@ def test_reference_arm_under_torchrun_prints_one_line():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_oracle_plan_large_workload_uses_all_cores_in_one_process():
+    """A workload whose oracle sample is tens of seconds on one core is timed as whole
+    samples in one process with BLAS on every core (cores = the threads used)."""
+    import numpy as np
+
+    from paper_2109_07358_gb300 import workloads as w
+
+    U = w.haar(2048, 512, seed=1)  # L N^2 x 4 = 2.1e9 multiply-adds: the large-workload plan
+    n, threads = bench.oracle_plan(U, 8, target_s=0.5)
+    assert threads == (os.cpu_count() or 1) and 1 <= n <= 8
+    rate, wall, cores = bench.oracle_baseline(U, 1, threads=threads)
+    assert rate > 0 and wall > 0 and cores == threads
+    small = w.chain_L64_N8()
+    n, threads = bench.oracle_plan(small, 100, target_s=0.2)
+    assert threads == 1 and n >= 2

@@ -9,6 +9,12 @@ compute one sample at a time.
   for the chosen residual form (1e-4) and the FP32 path (1e-6).
 * Anderson chain (L = 16384, N = 2048, real): teacher-forced conditionals of two
   samples, per residual precision, against the FP64 oracle; the error table is printed.
+  Free running at the benchmark's size and form (B = 8192, two waves of the 34 MB
+  per-sample state): no site twice in any sample, and four sampled indices spread over
+  both waves identical to the oracle's free-running samples except at boundary cases
+  within the excusal window.
+Excusal windows are the CDF errors measured teacher-forced on the same samples (floor
+1e-6; tests/parity_util.py).
 """
 import numpy as np
 import pytest
@@ -16,7 +22,8 @@ import torch
 
 from paper_2109_07358_gb300 import ffs
 from paper_2109_07358_gb300 import workloads as w
-from tests.parity_util import draw_identity, oracle_runs_parallel
+from tests.parity_util import (cdf_error, draw_identity, forced_draw_identity, forced_probs, oracle_runs_at,
+                               oracle_runs_parallel, window)
 
 pytestmark = pytest.mark.gpu
 
@@ -47,10 +54,18 @@ def test_lattice_full_batch_draws(lattice):
     S.close()
     assert ((X >= 0) & (X < U.shape[0])).all()
     assert (np.diff(np.sort(X, axis=1), axis=1) > 0).all()  # no site twice in any sample
-    frac, bad = draw_identity(X[:16], recs, eps=1e-4)
+    S = ffs.Sampler(torch.from_numpy(U).cuda(), BENCH_FORM)
+    P = forced_probs(S, recs, 0)
+    S.close()
+    meas = cdf_error(P, recs)
+    eps = window(meas, False)
+    frac, bad = draw_identity(X[:16], recs, eps=eps)
+    fd, nd = forced_draw_identity(P, recs)
     # a whole sample is 1024 chained draws: one boundary case anywhere changes the rest
-    print(f"lattice 64x64 full batch: {frac:.3f} of sampled whole samples identical, unexcused {bad}")
+    print(f"lattice 64x64 full batch: {frac:.3f} of sampled whole samples identical, teacher-forced draws "
+          f"{fd:.5f} of {nd}, measured CDF error {meas:.2e}, eps {eps:.2e}, unexcused {bad}")
     assert not bad
+    assert fd >= 0.999
 
 
 @pytest.mark.parametrize("flags,tol", [(CHOSEN, 1e-4), (ffs.FFS_RES_FP32 | ffs.FFS_STATE_DF64, 1e-6)])
@@ -97,3 +112,26 @@ def test_anderson_precision_table():
         if tol is not None:
             assert err <= tol, (name, err)
     print("Anderson L=16384 N=2048 max |dP| vs FP64 oracle:", {k: f"{v:.2e}" for k, v in table.items()})
+
+
+def test_anderson_full_batch_free_running():
+    """B = 8192 in the benchmark's form; indices 0, 1 (first wave) and 4097, 8191 (second
+    wave, when the batch runs in two) against the oracle's free-running samples."""
+    U = w.anderson_L16384_N2048(0)
+    idx = [0, 1, 4097, 8191]
+    recs = oracle_runs_at(U, 0, idx)
+    S = ffs.Sampler(torch.from_numpy(U).cuda(), CHOSEN)
+    X = S.sample(8192, 0)["x"].cpu().numpy()
+    S.sync()
+    assert ((X >= 0) & (X < U.shape[0])).all()
+    assert (np.diff(np.sort(X, axis=1), axis=1) > 0).all()  # no site twice in any sample
+    P = [forced_probs(S, [r], 0, first=s)[0] for s, r in zip(idx, recs)]
+    S.close()
+    meas = cdf_error(P, recs)
+    eps = window(meas, False)
+    frac, bad = draw_identity(X[idx], recs, eps=eps)
+    fd, nd = forced_draw_identity(P, recs)
+    print(f"Anderson full batch: {frac:.3f} of sampled whole samples identical, teacher-forced draws {fd:.5f} "
+          f"of {nd}, measured CDF error {meas:.2e}, eps {eps:.2e}, unexcused {bad}")
+    assert not bad
+    assert fd >= 0.999

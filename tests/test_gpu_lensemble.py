@@ -20,7 +20,7 @@ from scipy.stats import chisquare
 from oracle import ffs_oracle as orc
 from paper_2109_07358_gb300 import ffs
 from paper_2109_07358_gb300 import workloads as w
-from tests.parity_util import excused
+from tests.parity_util import cdf_error, excused, window
 
 pytestmark = pytest.mark.gpu
 
@@ -78,17 +78,6 @@ def test_parity(case, mode, tol):
         assert np.array_equal(P[b, :nb], r["m_full"])
         assert np.array_equal(P[b, nb:], np.setdiff1d(np.arange(N), r["kept"]))
         assert np.all(X[b, nb:] == -1)
-    # free-running draws: identical up to excused boundary cases
-    bad = []
-    same = 0
-    for b, r in enumerate(recs):
-        d = np.nonzero(X[b, :n[b]] != r["x"])[0]
-        if d.size == 0:
-            same += 1
-        elif not excused(r, int(d[0]), X[b, d[0]], tol):
-            bad.append((b, int(d[0])))
-    assert not bad, bad
-    assert same >= 0.95 * B
     # teacher forcing on the oracle's draws: conditionals, zero rows past each chain
     force = np.full((B, N), -1, dtype=np.int32)
     for b, r in enumerate(recs):
@@ -106,6 +95,21 @@ def test_parity(case, mode, tol):
             assert abs(lp[b] - r["logp"]) <= 1e-3 * max(1.0, abs(r["logp"]))
         assert not Pr[b, nb:].any()
     S.close()
+    # free-running draws: identical up to boundary cases within the excusal window (1e-6 on
+    # the FP32 path, else the CDF error measured on these teacher-forced conditionals)
+    meas = cdf_error([Pr[b, :r["kept"].size] for b, r in enumerate(recs)], recs)
+    eps = window(meas, mode == "fp32")
+    bad = []
+    same = 0
+    for b, r in enumerate(recs):
+        d = np.nonzero(X[b, :n[b]] != r["x"])[0]
+        if d.size == 0:
+            same += 1
+        elif not excused(r, int(d[0]), X[b, d[0]], eps):
+            bad.append((b, int(d[0])))
+    print(f"L-ensemble {case} {mode}: measured CDF error {meas:.2e}, eps {eps:.2e}")
+    assert not bad, bad
+    assert same >= 0.95 * B
     print(f"L-ensemble {case} {mode}: max |dP| {err:.2e}, chain lengths {n.min()}..{n.max()}, "
           f"identical samples {same}/{B}")
     assert err <= tol

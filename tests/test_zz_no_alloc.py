@@ -80,14 +80,14 @@ def test_noalloc_refuses_host_buffers():
     returns FFS_E_ARG for host memory (called through the C ABI, past the binding)."""
     import ctypes
 
-    U = torch.from_numpy(w.haar(40, 6, seed=2)).cuda()
+    U = torch.from_numpy(w.haar(40, 6, seed=2, complex_=False)).cuda()
     host_out = np.zeros((4, 6), dtype=np.int32)
     lib = ffs.lib()
     rc = lib.ffs_sample_noalloc(ctypes.c_void_p(U.data_ptr()), ffs.FFS_F64, 40, 6, 4, 0,
                                 ctypes.c_void_p(host_out.ctypes.data), None)
     assert rc == ffs.FFS_E_ARG
     assert "device" in lib.ffs_last_error(None).decode()
-    host_U = np.ascontiguousarray(w.haar(40, 6, seed=2))
+    host_U = np.ascontiguousarray(w.haar(40, 6, seed=2, complex_=False))
     dev_out = torch.empty((4, 6), dtype=torch.int32, device="cuda")
     rc = lib.ffs_sample_noalloc(ctypes.c_void_p(host_U.ctypes.data), ffs.FFS_F64, 40, 6, 4, 0,
                                 ctypes.c_void_p(dev_out.data_ptr()), None)
@@ -101,7 +101,7 @@ def test_noalloc_marks_degenerate_chains_with_minus_one():
     normaliser is 0): that entry and the rest of the row are -1, the earlier entries are
     distinct sites.  The step is known in advance from the sample's column order."""
     L, N, B, seed, zero_col = 40, 6, 64, 3, 2
-    Un = w.haar(L, N, seed=4)
+    Un = w.haar(L, N, seed=4, complex_=False)
     Un[:, zero_col] = 0.0
     U = torch.from_numpy(np.ascontiguousarray(Un)).cuda()
     out = torch.full((B, N), 7, dtype=torch.int32, device="cuda")
