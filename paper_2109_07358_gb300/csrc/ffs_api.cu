@@ -174,6 +174,7 @@ static void release(ffs_ctx* c) {
   cudaFree(c->sel_p);
   cudaFree(c->Ug);
   cudaFree(c->oz_buf);
+  cudaFree(c->ozy_buf);
   cudaFree(c->status);
   if (c->status_host) cudaFreeHost(c->status_host);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -309,6 +310,7 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
       CREATE_TRY(configure_residual_tc());
       CREATE_TRY(configure_blocked());
       CREATE_TRY(configure_oz());
+      CREATE_TRY(configure_oz_y());
       configured[c->device] = true;
     }
   }
@@ -409,6 +411,7 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
   const bool plain = op == kOpNone;
   const bool grouped = grouped_form(h);
   const bool tc_top = (h->flags & FFS_TRAILING_TC) && blocked(h);
+  const bool tc_new = tc_top && !h->cplx;  // the new rows (Y, Bot) on the tensor cores too
   const int64_t G = FFS_GROUP_SIZE;
   if (grouped && (first_sample_index % G) != 0)
     return fail(h, FFS_E_ARG, "grouped form: first_sample_index must be a multiple of 128");
@@ -428,6 +431,7 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
   if (out_probs && !probs_dev) per += (size_t)ldx * h->L * 4;
   if (grouped) per += group_copy_bytes(h) / G + 1;  // a group's operand copy, shared by its 128 samples
   if (tc_top) per += oz_bytes_per_sample(n_steps);   // slices of the tensor-core trailing update
+  if (tc_new) per += ozy_bytes_per_sample(n_steps);  // C's slices of the tensor-core new rows
   size_t free_b = 0, total_b = 0;
   FFS_CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t reserve = (size_t)512 << 20;
@@ -457,6 +461,7 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
     if (r != FFS_OK) return r;
   }
   if (tc_top) FFS_CUDA_TRY(h, oz_prepare(h, Bw, n_steps));
+  if (tc_new) FFS_CUDA_TRY(h, ozy_prepare(h, Bw, n_steps));
   int32_t* xbuf = nullptr;
   int32_t* fbuf = nullptr;
   float* pbuf = nullptr;
@@ -544,7 +549,10 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
         if (k + 1 == k1 && k1 < n_steps) {
           TIMED(h, FFS_PHASE_PANEL_S, st, launch_blocked_panel_s(a, bt, k0, k1, state_kind(h), st));
           bt.tc_top = tc_top ? 1 : 0;  // then the old rows and the next operand are the tensor-core pass's
-          TIMED(h, FFS_PHASE_PANEL, st, launch_blocked_panel_update(a, bt, k0, k1, state_kind(h), op, st));
+          if (tc_new)
+            TIMED(h, FFS_PHASE_PANEL, st, launch_oz_y(h, a, bt, k0, k1, st));
+          else
+            TIMED(h, FFS_PHASE_PANEL, st, launch_blocked_panel_update(a, bt, k0, k1, state_kind(h), op, st));
           if (tc_top) TIMED(h, FFS_PHASE_PANEL_TC, st, launch_oz_top(h, a, bt, k0, k1, op, st));
           bt.tc_top = 0;
         }

@@ -146,6 +146,14 @@ struct OzArgs {
   int64_t KP, TP;
 };
 
+// C's slices for the tensor-core new-row update (real state): [b][chunk][slice][32][64]
+// BF16 and the row scales [b][chunk][32]; n_chunks = chunks of 64 old rows per sample.
+struct OzYArgs {
+  __nv_bfloat16* C;
+  float* Cs;
+  int64_t n_chunks;
+};
+
 // ------------------------------------------------------------------ status word
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
@@ -210,6 +218,12 @@ struct ffs_ctx {
   fermi::OzArgs oz{};
   CUtensorMap ozA, ozB;
   int64_t oz_key_B = -1, oz_key_Nc = -1;
+  // Tensor-core new-row update (FFS_TRAILING_TC, real U): C's slices and their tensor map.
+  void* ozy_buf = nullptr;
+  size_t ozy_bytes = 0;
+  fermi::OzYArgs ozy{};
+  CUtensorMap ozyC;
+  int64_t ozy_key_B = -1, ozy_key_Nc = -1;
   // Grouped form: per group of 128 samples a copy of the residual operand planes with the
   // K columns in the group's order ([planes][groups][Lrp][Kp]) and its tensor maps.
   void* Ug = nullptr;

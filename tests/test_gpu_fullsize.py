@@ -28,7 +28,7 @@ from tests.parity_util import (cdf_error, draw_identity, forced_draw_identity, f
 pytestmark = pytest.mark.gpu
 
 CHOSEN = ffs.FFS_RES_BF16X3 | ffs.FFS_STATE_DF64
-BENCH_FORM = CHOSEN | ffs.FFS_TRAILING_TC  # what bench.py times on complex U
+BENCH_FORM = CHOSEN | ffs.FFS_TRAILING_TC  # what bench.py times
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -99,8 +99,8 @@ def test_anderson_precision_table():
     recs = oracle_runs_parallel(U, 0, 0, 2)
     force = torch.tensor(np.stack([r["x"] for r in recs]), dtype=torch.int32, device="cuda")
     table = {}
-    modes = {"bf16x3": (ffs.FFS_RES_BF16X3, 1e-4), "tf32": (ffs.FFS_RES_TF32, None), "bf16": (ffs.FFS_RES_BF16, None),
-             "fp32": (ffs.FFS_RES_FP32, 1e-6)}
+    modes = {"bf16x3": (ffs.FFS_RES_BF16X3, 1e-4), "bf16x3_tc": (ffs.FFS_RES_BF16X3 | ffs.FFS_TRAILING_TC, 1e-4),
+             "tf32": (ffs.FFS_RES_TF32, None), "bf16": (ffs.FFS_RES_BF16, None), "fp32": (ffs.FFS_RES_FP32, 1e-6)}
     Ud = torch.from_numpy(U).cuda()
     for name, (res, tol) in modes.items():
         S = ffs.Sampler(Ud, res | ffs.FFS_STATE_DF64)
@@ -120,7 +120,7 @@ def test_anderson_full_batch_free_running():
     U = w.anderson_L16384_N2048(0)
     idx = [0, 1, 4097, 8191]
     recs = oracle_runs_at(U, 0, idx)
-    S = ffs.Sampler(torch.from_numpy(U).cuda(), CHOSEN)
+    S = ffs.Sampler(torch.from_numpy(U).cuda(), BENCH_FORM)
     X = S.sample(8192, 0)["x"].cpu().numpy()
     S.sync()
     assert ((X >= 0) & (X < U.shape[0])).all()

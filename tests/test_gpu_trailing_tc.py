@@ -24,6 +24,9 @@ CASES = {
     "lattice": lambda: w.square_lattice(16, 16, 100, seed=3),
     "real_tiles": lambda: w.haar(1000, 300, seed=13, complex_=False),
     "anderson": lambda: w.anderson_chain(2048, 200, 1.0, seed=2),
+    # k0 up to 608: ten 64-row chunks per new-row product, so every ring of the tensor-core
+    # kernels wraps several times
+    "real_long": lambda: w.haar(1500, 640, seed=14, complex_=False),
 }
 
 

@@ -149,3 +149,92 @@ def test_subnormal_row_maximum_keeps_finite_exact_slices():
     _, e = np.frexp(F(3e-40))
     with np.errstate(over="ignore"):
         assert not np.isfinite(F(np.ldexp(F(1.0), -int(e))))
+
+
+def slices_fast(hi, lo):
+    """The new-row kernel's slicing step: the remainder pair is renormalised with the fast
+    two-sum (s = d + tl, e = tl - (s - d)); each step is checked to be error-free."""
+    th, tl = F(hi * F(128)), F(lo * F(128))
+    out = []
+    for _ in range(SLICES):
+        a = F(np.rint(th))
+        d = F(th - a)
+        assert Fraction(float(d)) == Fraction(float(th)) - Fraction(float(a))   # exact difference
+        s = F(d + tl)
+        e = F(tl - F(s - d))
+        assert Fraction(float(s)) + Fraction(float(e)) == Fraction(float(d)) + Fraction(float(tl))  # error-free
+        out.append(a)
+        th, tl = F(s * F(256)), F(e * F(256))
+    return out, Fraction(float(th)) + Fraction(float(tl))
+
+
+def adversarial_df(rng, n):
+    """Double-float values at the edges of the fast two-sum's condition: lo at +-ulp(hi)/2,
+    hi with few significant bits or integral after scaling, tiny and zero lo."""
+    hi = rng.standard_normal(n).astype(F)
+    hi[: n // 4] = np.round(hi[: n // 4] * 64) / 64            # few significant bits
+    ulp = np.spacing(np.abs(hi)).astype(F)
+    lo = (rng.choice([-0.5, 0.5, 0.25, -0.125, 0.0], n) * ulp).astype(F)
+    lo[n // 2: n // 2 + 4] = F(1e-40)                           # subnormal low parts
+    return hi, lo
+
+
+@pytest.mark.parametrize("gen", ["random", "adversarial"])
+def test_fast_two_sum_slicing_is_exact(gen):
+    rng = np.random.default_rng(7)
+    hi, lo = random_df(rng, 256) if gen == "random" else adversarial_df(rng, 256)
+    sigma, inv = pow2_scale(float(np.max(np.abs(hi))))
+    for h, l in zip(hi, lo):
+        s, rem = slices_fast(F(h * inv), F(l * inv))
+        for a in s:
+            assert float(a).is_integer() and abs(a) <= 128
+        recon = sum(Fraction(int(a)) * Fraction(1, 2 ** (7 + 8 * i)) for i, a in enumerate(s))
+        remainder = rem * Fraction(1, 2 ** (7 + 8 * SLICES))
+        assert recon + remainder == exact(F(h * inv), F(l * inv))
+        assert abs(remainder) <= Fraction(1, 2 ** 48)
+
+
+def test_chunked_new_row_product_error():
+    """One 64-row chunk of Y's product sum_j W[j, c] C[i, j] as the kernel forms it: per
+    (column, chunk) and (row, chunk) power-of-two scales, six fast-two-sum slices each,
+    the 26 products with i + j <= 8 summed in FP32 per group (integers below 2^21), groups
+    added with weights 2^(-8(d-2)) and the scales: within 2^-46 sigma_c sigma_i K of the
+    exact rational product."""
+    rng = np.random.default_rng(11)
+    for scale_w, scale_c in ((1.0, 1.0), (30.0, 1e-3), (1e-30, 5.0)):
+        wh, wl = random_df(rng, K, scale_w)
+        ch, cl = random_df(rng, K, scale_c)
+        sw, iw = pow2_scale(float(np.max(np.abs(wh))))
+        sc, ic = pow2_scale(float(np.max(np.abs(ch))))
+        A = [slices_fast(F(h * iw), F(l * iw))[0] for h, l in zip(wh, wl)]
+        Bm = [slices_fast(F(h * ic), F(l * ic))[0] for h, l in zip(ch, cl)]
+        total = Fraction(0)
+        for d in range(2, DMAX + 1):
+            acc = F(0)
+            for k in range(K):
+                for i in range(1, SLICES + 1):
+                    j = d - i
+                    if 1 <= j <= SLICES:
+                        acc = F(acc + F(A[k][i - 1] * Bm[k][j - 1]))
+                        assert float(acc).is_integer() and abs(acc) < 2 ** 21
+            total += Fraction(float(acc)) * Fraction(1, 2 ** (8 * (d - 2)))
+        approx = total * Fraction(float(sw)) * Fraction(float(sc)) / 2 ** 14
+        truth = sum(exact(a, b) * exact(c, e) for a, b, c, e in zip(wh, wl, ch, cl))
+        bound = Fraction(float(sw)) * Fraction(float(sc)) * K / 2 ** 46
+        assert abs(approx - truth) <= bound, (scale_w, scale_c, float(abs(approx - truth) / bound))
+
+
+def test_smallest_scale_keeps_the_scaling_finite():
+    """A column chunk whose largest entry is far below FP32's normal range takes the floor
+    scale sigma = 2^-125; x / sigma is formed first and then multiplied by 2^7, because the
+    single factor 2^125 x 2^7 would overflow FP32 (and 0 x inf would turn zero entries into
+    NaN).  The slices of such values stay finite, exact and sum to x / sigma."""
+    sigma, inv = pow2_scale(1e-40)
+    with np.errstate(over="ignore"):
+        assert float(inv) == 2.0 ** 125 and not np.isfinite(F(inv * F(128)))   # the factor that overflows
+    for h in (F(1e-40), F(0.0), F(-3e-39), F(1.2e-38)):
+        th, tl = F(F(h * inv) * F(128)), F(F(F(0.0) * inv) * F(128))
+        assert np.isfinite(th) and np.isfinite(tl)
+        s, rem = slices_fast(F(h * inv), F(0.0))
+        recon = sum(Fraction(int(a)) * Fraction(1, 2 ** (7 + 8 * i)) for i, a in enumerate(s))
+        assert recon + rem * Fraction(1, 2 ** (7 + 8 * SLICES)) == Fraction(float(F(h * inv)))
