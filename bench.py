@@ -54,6 +54,10 @@ WORKLOADS = {
         desc="1D open Anderson chain L=16384, on-site disorder U[-1, 1] (seed 0), N=2048 lowest orbitals, "
              "real, B=8192 samples, Philox seed 0 (the precision workload; the per-sample state is 34 MB, "
              "so the batch runs in waves)"),
+    "anderson_L4096_N512_B2048": dict(
+        make="anderson4k", B=2048, L=4096, N=512, cplx=False, grid=(1, 4096),
+        desc="1D open Anderson chain L=4096, on-site disorder U[-1, 1] (seed 0), N=512 lowest orbitals, real, "
+             "B=2048 samples, Philox seed 0 (reduced case for profiler captures)"),
     "chain64_N8_B10000": dict(
         make="chain", B=10000, L=64, N=8, cplx=False, grid=(1, 64),
         desc="1D open chain L=64, N=8 (closed-form orbitals), B=10^4 samples, Philox seed 0"),
@@ -67,12 +71,13 @@ L2_BYTES = 129 * 2**20
 
 
 def working_set_bytes(L, N, B, cplx, state):
-    """Bytes one step touches: the per-sample blocked state (N x round_up(N, 32) entries),
-    U in FP64 and its BF16 hi/lo copies, the output rows."""
+    """Bytes one step touches: the per-sample blocked state (slab s of 32 columns holds
+    32 (s + 1) rows: 512 S (S + 1) entries for S = ceil(N / 32) slabs), U in FP64 and its
+    BF16 hi/lo copies, the output rows."""
     entry = {"df64": 8, "fp64": 8, "fp32": 4}[state] * (2 if cplx else 1)
-    ncp = (N + 31) // 32 * 32
+    S = (N + 31) // 32
     u = L * N * (2 if cplx else 1) * (8 + 4)
-    return B * N * ncp * entry + u + B * N * 4
+    return B * 512 * S * (S + 1) * entry + u + B * N * 4
 
 
 def load_peaks():
@@ -96,6 +101,8 @@ def make_U(spec):
         return w.chain_L64_N8()
     if spec["make"] == "anderson":
         return w.anderson_L16384_N2048(0)
+    if spec["make"] == "anderson4k":
+        return w.anderson_chain(4096, 512, 1.0, 0)
     raise ValueError(spec["make"])
 
 

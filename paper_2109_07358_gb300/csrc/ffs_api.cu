@@ -88,7 +88,7 @@ static size_t state_elem_bytes(const ffs_ctx* c) { return blocked_elem_bytes(c->
 static size_t state_cols(const ffs_ctx* c, int64_t Nc) { return blocked(c) ? (size_t)Nc : (size_t)c->N; }
 static size_t state_entries(const ffs_ctx* c, int64_t Nc) {
   const size_t sc = state_cols(c, Nc);
-  return blocked(c) ? sc * ((sc + 31) / 32 * 32) : sc * sc;
+  return blocked(c) ? (size_t)state_stride((int64_t)sc) : sc * sc;
 }
 static size_t per_sample_bytes_nc(const ffs_ctx* c, int64_t Nc) {
   const int op = op_mode_of(c->flags);
@@ -687,8 +687,8 @@ int ffs_sample_metropolis(ffs_handle h, int64_t B, uint64_t seed, uint64_t first
   const int state = state_kind(h);
   const size_t es = state_elem_bytes(h), nb = blocked_panel_width(), Nc = (size_t)n_steps;
   // per sample: m, drawn-site bits, the blocked state (no residual operand, no weights)
-  const size_t Ncp = (Nc + 31) / 32 * 32;  // the state is stored in 32-column slabs
-  const size_t per = (size_t)h->N * 4 + (size_t)h->ldMask * 4 + (Nc * Ncp + Nc * nb + nb * nb) * es;
+  const size_t st_entries = (size_t)state_stride((int64_t)Nc);  // the blocked state's slabs
+  const size_t per = (size_t)h->N * 4 + (size_t)h->ldMask * 4 + (st_entries + Nc * nb + nb * nb) * es;
   size_t free_b = 0, total_b = 0;
   FFS_CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t reserve = (size_t)512 << 20;
@@ -700,7 +700,7 @@ int ffs_sample_metropolis(ffs_handle h, int64_t B, uint64_t seed, uint64_t first
   void *W = nullptr, *W0P = nullptr, *Sinv = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&m, (size_t)Bw * h->N * 4, st);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&mask, (size_t)Bw * h->ldMask * 4, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&W, (size_t)Bw * Nc * Ncp * es, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&W, (size_t)Bw * st_entries * es, st);
   if (e == cudaSuccess) e = cudaMallocAsync(&W0P, (size_t)Bw * Nc * nb * es, st);
   if (e == cudaSuccess) e = cudaMallocAsync(&Sinv, (size_t)Bw * nb * nb * es, st);
   for (int64_t b0 = 0; b0 < B && e == cudaSuccess; b0 += Bw) {

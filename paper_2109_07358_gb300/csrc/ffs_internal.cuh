@@ -217,6 +217,7 @@ struct ffs_ctx {
   size_t oz_bytes = 0;
   fermi::OzArgs oz{};
   CUtensorMap ozA, ozB;
+  CUtensorMap ozA2, ozB2;  // real states: the packed pair layouts of the same buffers
   int64_t oz_key_B = -1, oz_key_Nc = -1;
   // Tensor-core new-row update (FFS_TRAILING_TC, real U): C's slices and their tensor map.
   void* ozy_buf = nullptr;

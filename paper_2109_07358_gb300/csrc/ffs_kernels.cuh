@@ -48,6 +48,17 @@ __device__ __forceinline__ int operand_col(const StepArgs& a, const int32_t* mro
   return a.grouped ? (int)j : mrow[j];
 }
 
+// Layout of a sample's blocked elimination state.  The columns are stored in slabs of 32;
+// slab s (columns [32 s, 32 s + 32)) holds only the rows it can ever hold, 0 .. 32 s + 31
+// (column c is live while at most c fermions are placed, so its rows stay below
+// 32 (c / 32 + 1)), contiguously with 32 entries per row: element (j, c) sits at
+// slab_offset(c / 32) + 32 j + c % 32, and a sample holds slab_offset(ceil(Nc / 32))
+// entries, about half of Nc^2.  The columns of one slab over a range of rows, which the
+// per-step and per-panel kernels stream, are one run of memory.
+__host__ __device__ __forceinline__ int64_t slab_offset(int64_t s) { return 512 * s * (s + 1); }
+__host__ __device__ __forceinline__ int64_t state_stride(int64_t Nc) { return slab_offset((Nc + 31) / 32); }
+__host__ __device__ __forceinline__ int64_t sidx(int64_t j, int64_t c) { return slab_offset(c >> 5) + j * 32 + (c & 31); }
+
 // Precision of the per-sample elimination state.
 enum StateKind : int { kStateFP64 = 0, kStateFP32 = 1, kStateDF64 = 2 };
 

@@ -93,7 +93,7 @@ __device__ __forceinline__ void pow2_scale(float mx, float& sigma, float& inv) {
   }
   int e;
   frexpf(mx, &e);  // mx = m 2^e, m in [0.5, 1): mx < 2^e
-  e = max(e, -125);
+  e = min(max(e, -125), 127);  // at 2^127: |v| / sigma < 2, first slice <= 256 (exact in BF16)
   sigma = ldexpf(1.f, e);
   inv = ldexpf(1.f, -e);
 }
@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(256) oz_slice_b_kernel(StepArgs a, BlockedArgs
   const int64_t c = k1 + (int64_t)blockIdx.x * 8 + warp;
   if (c >= t.Nc) return;
   if (a.nlen && a.nlen[b] <= k1) return;
-  const int64_t Nc = t.Nc, Ncp = (Nc + 31) & ~(int64_t)31;
-  const size_t idx = (size_t)b * Nc * Ncp + ((c >> 5) * Nc + k0 + lane) * 32 + (c & 31);
+  const int64_t Nc = t.Nc;
+  const size_t idx = (size_t)b * state_stride(Nc) + sidx(k0 + lane, c);
   df vre, vim = df{0.f, 0.f};
   if constexpr (CX) {
     const cdf v = ((const cdf*)t.W)[idx];
@@ -300,7 +300,6 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
     const int64_t j = mt * MT + 32 * q + lane;
     const bool live_row = j < k0;
     const float sr = live_row ? z.As[(size_t)b * z.KP + j] : 1.f;
-    const int64_t Ncp = (Nc + 31) & ~(int64_t)31;
     uint8_t* Pq = pstage + (size_t)q * 32 * kPRow;  // the quarter's 32 rows
     // All warps of a quarter pass the two quarter barriers of every slab even after a wait
     // has failed (they then skip the work), so that none can be left at a barrier.
@@ -337,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
       __syncwarp();
       if (lane == 0 && ok) mbar_arrive(acc_empty);  // the accumulators may be overwritten now
       named_sync(quarter_bar, quarter_threads);     // all the quarter's columns are staged
-      const size_t slab = (size_t)b * Nc * Ncp + (size_t)(c0 >> 5) * Nc * 32;
+      const size_t slab = (size_t)b * state_stride(Nc) + (size_t)slab_offset(c0 >> 5);
       const bool col_ok = ok && c0 + lane < Nc;
 #pragma unroll
       for (int rr = kEpiCols * h; rr < kEpiCols * h + kEpiCols; ++rr) {
@@ -355,6 +354,240 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
             Wc[jr * 32 + lane] = df_sub(Wc[jr * 32 + lane], p.re);
           }
         }
+      }
+      named_sync(quarter_bar, quarter_threads);  // before the next slab overwrites the staging rows
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ------------------------------------------------------------------ real states: packed pairs
+// For a real state the panel dimension K is 32, half of a 128-byte operand row.  Instead of
+// padding each slice row with zeros, two slices share one row: A rows hold the pairs
+// [a_p | a_p+1] (p = 1, 3, 5), B rows the shifted pairs [b_q | b_q-1] (q = 1 .. 7, b_0 =
+// b_7 = 0), so that one K = 64 product [a_p | a_p+1] . [b_q | b_q-1] = a_p b_q + a_p+1 b_q-1
+// adds two slice products of the same weight d = p + q.  The 26 products with d <= 8 take 15
+// packed products (60 MMAs per 128 x 32 tile instead of 104); each accumulator still sums 64
+// products below 2^14, so it stays exact.  The accumulators are double-buffered (2 x 7
+// groups x 32 columns), so a slab's epilogue overlaps the next slab's products.
+constexpr int kPairA = 3, kPairB = 7;
+constexpr uint32_t kRABytes = kPairA * kATile;       // 48 KB
+constexpr uint32_t kRBStage = kPairB * kBTile;       // 28 KB: the seven pair tiles of a slab
+constexpr int kRBStages = 3;
+constexpr uint32_t kRPRow = NT * 8 + 16;             // staged row: 32 double-floats + pad
+constexpr uint32_t kRPStage = 4 * 32 * kRPRow;
+constexpr uint32_t kRSmem = kRABytes + kRBStages * kRBStage + kRPStage + 1024 + 256;
+constexpr uint32_t kRAccCols = 256;                  // one accumulator set (7 x 32 columns used)
+
+// A pairs: row r < k0 of W0_P; layout [b][pair][KP][64] BF16, sigma_r in As[b][KP].
+__global__ void __launch_bounds__(256) oz_pair_a_kernel(StepArgs a, BlockedArgs t, OzArgs z, int64_t k0,
+                                                        int64_t k1) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;  // lane = panel column
+  const int64_t b = blockIdx.y;
+  const int64_t r = (int64_t)blockIdx.x * 8 + warp;
+  if (r >= k0) return;
+  if (a.nlen && a.nlen[b] <= k1) return;
+  const df w = ((const df*)t.W0P)[((size_t)b * t.Nc + r) * 32 + lane];
+  float sigma, inv;
+  pow2_scale(warp_max(fabsf(w.hi)), sigma, inv);
+  float sl[kSlices];
+  df_slices(df_scale(w, inv), sl);
+  __nv_bfloat16* A = z.A + (size_t)b * kPairA * z.KP * 64;
+#pragma unroll
+  for (int p = 0; p < kPairA; ++p) {
+    __nv_bfloat16* row = A + ((size_t)p * z.KP + r) * 64;
+    row[lane] = __float2bfloat16_rn(sl[2 * p]);
+    row[32 + lane] = __float2bfloat16_rn(sl[2 * p + 1]);
+  }
+  if (lane == 0) z.As[(size_t)b * z.KP + r] = sigma;
+}
+
+// B shifted pairs: trailing column c of Bot (state rows k0 .. k0+31); layout
+// [b][slab][pair][32 columns][64] BF16 (slab = (c - k1) / 32), sigma_c in Bs[b][TP].
+__global__ void __launch_bounds__(256) oz_pair_b_kernel(StepArgs a, BlockedArgs t, OzArgs z, int64_t k0,
+                                                        int64_t k1) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;  // lane = panel row
+  const int64_t b = blockIdx.y;
+  const int64_t c = k1 + (int64_t)blockIdx.x * 8 + warp;
+  if (c >= t.Nc) return;
+  if (a.nlen && a.nlen[b] <= k1) return;
+  const df v = ((const df*)t.W)[(size_t)b * state_stride(t.Nc) + sidx(k0 + lane, c)];
+  float sigma, inv;
+  pow2_scale(warp_max(fabsf(v.hi)), sigma, inv);
+  float sl[kSlices];
+  df_slices(df_scale(v, inv), sl);
+  const int64_t nt = (c - k1) >> 5, rr = (c - k1) & 31;
+  __nv_bfloat16* B = z.B + ((size_t)b * (z.TP / NT) + nt) * kPairB * NT * 64;
+#pragma unroll
+  for (int q = 1; q <= kPairB; ++q) {
+    __nv_bfloat16* row = B + ((size_t)(q - 1) * NT + rr) * 64;
+    row[lane] = __float2bfloat16_rn(q <= kSlices ? sl[q - 1] : 0.f);
+    row[32 + lane] = __float2bfloat16_rn(q >= 2 ? sl[q - 2] : 0.f);
+  }
+  if (lane == 0) z.Bs[(size_t)b * z.TP + c] = sigma;
+}
+
+// Top = W0_T - W0_P Bot for 128 old rows of one sample (real state), every trailing slab.
+__global__ void __launch_bounds__(kThreads, 1) oz_top_real_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                  const __grid_constant__ CUtensorMap tmB, StepArgs a,
+                                                                  BlockedArgs t, OzArgs z, int64_t k0, int64_t k1) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = blockIdx.y;
+  const int64_t mt = blockIdx.x;
+  if (a.nlen && a.nlen[b] <= k1) return;  // uniform over the CTA
+  const int64_t Nc = t.Nc;
+  const int n_tiles = (int)((Nc - k1 + NT - 1) / NT);
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (sbase - raw);
+  uint8_t* pstage = gbase + kRABytes + kRBStages * kRBStage;
+  uint64_t* bars = (uint64_t*)(pstage + kRPStage);
+  const uint32_t bar0 = smem_u32(bars);
+  const uint32_t a_full = bar0;
+  auto b_full = [&](int s) { return bar0 + 8u * (1 + s); };
+  auto b_empty = [&](int s) { return bar0 + 8u * (1 + kRBStages + s); };
+  auto acc_full = [&](int u) { return bar0 + 8u * (1 + 2 * kRBStages + u); };
+  auto acc_empty = [&](int u) { return bar0 + 8u * (3 + 2 * kRBStages + u); };
+  const uint32_t mma_done = bar0 + 8u * (5 + 2 * kRBStages);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 6 + 2 * kRBStages);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const uint32_t sA = sbase, sB = sbase + kRABytes;
+
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    for (int s = 0; s < kRBStages; ++s) {
+      mbar_init(b_full(s), 1);
+      mbar_init(b_empty(s), 1);
+    }
+    for (int u = 0; u < 2; ++u) {
+      mbar_init(acc_full(u), 1);
+      mbar_init(acc_empty(u), kEpiWarps);
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  auto fail = [&]() {
+    *abort_flag = 1;
+    set_status(a.status, FFS_E_TIMEOUT);
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA: the A pairs once, then the seven B pair tiles of every slab (one box)
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+    mbar_arrive_expect_tx(a_full, kRABytes);
+    for (int p = 0; p < kPairA; ++p)
+      tma_load_2d(sA + p * kATile, &tmA, a_full, 0, (int32_t)((b * kPairA + p) * z.KP + mt * MT));
+    const int64_t nslab = z.TP / NT;
+    int issued = 0;
+    for (int nt = 0; nt < n_tiles; ++nt) {
+      const int s = nt % kRBStages;
+      if (nt >= kRBStages && !mbar_wait(b_empty(s), ((nt / kRBStages) - 1) & 1, abort_flag)) {
+        fail();
+        break;
+      }
+      mbar_arrive_expect_tx(b_full(s), kRBStage);
+      tma_load_2d(sB + s * kRBStage, &tmB, b_full(s), 0, (int32_t)((b * nslab + nt) * kPairB * NT));
+      ++issued;
+    }
+    mbar_drain(a_full, 0, kSpinLimit);
+    for (int nt = (issued > kRBStages ? issued - kRBStages : 0); nt < issued; ++nt)
+      mbar_drain(b_full(nt % kRBStages), (nt / kRBStages) & 1, kSpinLimit);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: group d of accumulator set u at columns u * 256 + 32 (d - 2)
+    bool ok = mbar_wait(a_full, 0, abort_flag);
+    if (!ok) fail();
+    for (int nt = 0; nt < n_tiles && ok; ++nt) {
+      const int s = nt % kRBStages, u = nt & 1;
+      if ((nt >= 2 && !mbar_wait(acc_empty(u), ((nt >> 1) - 1) & 1, abort_flag)) ||
+          !mbar_wait(b_full(s), (nt / kRBStages) & 1, abort_flag)) {
+        fail();
+        break;
+      }
+      tc_fence_after();
+      const uint32_t stB = sB + s * kRBStage, accb = tmem + (uint32_t)u * kRAccCols;
+#pragma unroll 1
+      for (int p = 1; p <= 5; p += 2) {
+#pragma unroll 1
+        for (int q = 1; q <= kPairB && p + q <= kDmax; ++q) {
+          const int d = p + q;
+          const uint32_t ta = sA + ((p - 1) / 2) * kATile, tb = stB + (q - 1) * kBTile;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma_bf16(accb + (uint32_t)(32 * (d - 2)), smem_desc_sw128(ta + kk * 32), smem_desc_sw128(tb + kk * 32),
+                     kIdesc, (p > 1 || kk > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(b_empty(s));
+      mma_commit(acc_full(u));
+    }
+    mma_commit(mma_done);
+    mbar_drain(mma_done, 0, kSpinLimit);
+  } else if (warp >= 2) {
+    // ---- epilogue: thread = old row (its TMEM lane) and 8 columns while reading the
+    // accumulators, then lanes over columns while updating W0_T (8 rows per warp)
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
+    const uint32_t quarter_bar = 1 + q;
+    const uint32_t quarter_threads = 32 * (kEpiWarps / 4);
+    const int64_t j = mt * MT + 32 * q + lane;
+    const float sr = j < k0 ? z.As[(size_t)b * z.KP + j] : 1.f;
+    uint8_t* Pq = pstage + (size_t)q * 32 * kRPRow;
+    bool dead = false;
+    for (int nt = 0; nt < n_tiles; ++nt) {
+      const int u = nt & 1;
+      const bool ok = !dead && mbar_wait(acc_full(u), (nt >> 1) & 1, abort_flag);
+      if (!ok && !dead) {
+        fail();
+        dead = true;
+      }
+      const int64_t c0 = k1 + (int64_t)nt * NT;
+      if (ok) {
+        tc_fence_after();
+        df S[kEpiCols];
+#pragma unroll
+        for (int n = 0; n < kEpiCols; ++n) S[n] = df{0.f, 0.f};
+        for (int d = kDmax; d >= 2; --d) {  // smallest terms first
+          uint32_t r[kEpiCols];
+          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)u * kRAccCols + (uint32_t)(32 * (d - 2) + kEpiCols * h), r);
+          tmem_ld_wait();
+          const float p2 = ldexpf(1.f, -8 * (d - 2));
+#pragma unroll
+          for (int n = 0; n < kEpiCols; ++n) S[n] = df_add(S[n], df{__uint_as_float(r[n]) * p2, 0.f});
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty(u));  // the accumulators may be overwritten now
+#pragma unroll
+        for (int n = 0; n < kEpiCols; ++n) {
+          const int64_t c = c0 + kEpiCols * h + n;
+          const float scale = (c < Nc) ? sr * z.Bs[(size_t)b * z.TP + c] * 0x1p-14f : 0.f;
+          *(df*)(Pq + lane * kRPRow + (kEpiCols * h + n) * 8) = df_scale(S[n], scale);
+        }
+      }
+      named_sync(quarter_bar, quarter_threads);  // all the quarter's columns are staged
+      df* Wc = (df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c0 >> 5);
+      const bool col_ok = ok && c0 + lane < Nc;
+#pragma unroll
+      for (int rr = kEpiCols * h; rr < kEpiCols * h + kEpiCols; ++rr) {
+        const int64_t jr = mt * MT + 32 * q + rr;
+        if (jr < k0 && col_ok) Wc[jr * 32 + lane] = df_sub(Wc[jr * 32 + lane], *(const df*)(Pq + rr * kRPRow + lane * 8));
       }
       named_sync(quarter_bar, quarter_threads);  // before the next slab overwrites the staging rows
     }
@@ -400,6 +633,10 @@ cudaError_t oz_prepare(ffs_ctx* c, int64_t Bw, int64_t Nc) {
     c->oz.TP = TP;
     cudaError_t e = encode_2d(&c->ozA, c->oz.A, false, 64, (uint64_t)Bw * kSlices * KP, kARows);
     if (e == cudaSuccess) e = encode_2d(&c->ozB, c->oz.B, false, 64, (uint64_t)Bw * kSlices * 2 * TP, kBRows);
+    // real states: the packed pair layouts in the same buffers (A pairs [b][3][KP], one
+    // box of 128 rows; B shifted pairs [b][slab][7][32], one box = the seven tiles of a slab)
+    if (e == cudaSuccess) e = encode_2d(&c->ozA2, c->oz.A, false, 64, (uint64_t)Bw * kPairA * KP, kARows);
+    if (e == cudaSuccess) e = encode_2d(&c->ozB2, c->oz.B, false, 64, (uint64_t)Bw * (TP / NT) * kPairB * NT, kPairB * NT);
     if (e != cudaSuccess) return e;
     c->oz_key_B = Bw;
     c->oz_key_Nc = Nc;
@@ -419,9 +656,9 @@ cudaError_t launch_oz_top(ffs_ctx* c, const StepArgs& a, const BlockedArgs& t, i
       oz_slice_b_kernel<true><<<gb, 256, 0, s>>>(a, t, z, k0, k1);
       oz_top_kernel<true><<<gt, kThreads, kSmem, s>>>(c->ozA, c->ozB, a, t, z, k0, k1);
     } else {
-      oz_slice_a_kernel<false><<<ga, 256, 0, s>>>(a, t, z, k0, k1);
-      oz_slice_b_kernel<false><<<gb, 256, 0, s>>>(a, t, z, k0, k1);
-      oz_top_kernel<false><<<gt, kThreads, kSmem, s>>>(c->ozA, c->ozB, a, t, z, k0, k1);
+      oz_pair_a_kernel<<<ga, 256, 0, s>>>(a, t, z, k0, k1);
+      oz_pair_b_kernel<<<gb, 256, 0, s>>>(a, t, z, k0, k1);
+      oz_top_real_kernel<<<gt, kThreads, kRSmem, s>>>(c->ozA2, c->ozB2, a, t, z, k0, k1);
     }
   }
   cudaError_t e = cudaGetLastError();
@@ -433,6 +670,8 @@ cudaError_t configure_oz() {
   cudaError_t e = cudaFuncSetAttribute(oz_top_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(oz_top_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(oz_top_real_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRSmem);
   return e;
 }
 

@@ -58,9 +58,6 @@ constexpr uint32_t kYSmem = kYAHalves * kYAHalf + kYBStages * kYBStage + kYSigRi
 static_assert(YN * YM * 8 + YN * YN * 8 <= kYAHalves * kYAHalf, "Y and S^-1 staging fit the operand ring");
 constexpr uint32_t kYIdesc = idesc_bf16(YM, YN);
 
-// Entries per sample of the blocked state (Nc rows x round_up(Nc, 32) columns in slabs).
-__device__ __forceinline__ int64_t ystride(int64_t Nc) { return Nc * ((Nc + 31) & ~(int64_t)31); }
-
 // Power-of-two scale sigma > max (as sigma, 1/sigma); 1 for an all-zero chunk.  A
 // subnormal max takes sigma = 2^-125 so that 1/sigma stays finite; a max at or above
 // 2^127 takes sigma = 2^127 (then |x| / sigma < 2 and the first slice is at most 256,
@@ -277,7 +274,7 @@ __global__ void __launch_bounds__(kYThreads, 1)
     const int cl = pid >> 1, q = pid & 1;
     const int64_t c = c0 + cl;
     const bool cval = c < Nc;
-    const df* Wc = (const df*)t.W + (size_t)b * ystride(Nc) + (size_t)((c >> 5) * Nc) * 32 + (c & 31);
+    const df* Wc = (const df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
     for (int tc = 0; tc < nch; ++tc) {
       float th[32], tl[32];
       float mx = 0.f;
@@ -404,7 +401,7 @@ __global__ void __launch_bounds__(kYThreads, 1)
     for (int e = et; e < YN * YN; e += 32 * kYEpiWarps) Si[e] = ((const df*)t.Sinv)[(size_t)b * YN * YN + e];
     named_sync(1, 32 * kYEpiWarps);
     if (cval) {
-      df* Wn = (df*)t.W + (size_t)b * ystride(Nc) + (size_t)((c >> 5) * Nc) * 32 + (c & 31);
+      df* Wn = (df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
 #pragma unroll 1
       for (int n = 0; n < 16; ++n) {
         const int i = 16 * hh + n;

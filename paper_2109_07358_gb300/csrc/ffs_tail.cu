@@ -23,11 +23,8 @@
 //   In exact arithmetic this is the same state the per-step updates would produce.
 // Only the first Nc = n_steps columns are kept (marginal sampling needs no more).
 //
-// Layout of a sample's state: the columns are stored in slabs of 32; slab s holds rows
-// 0..Nc-1 of columns [32 s, 32 s + 32) contiguously, so element (j, c) sits at
-// (c / 32 * Nc + j) * 32 + c % 32 (Nc x round_up(Nc, 32) entries per sample).  The
-// columns of a panel over a range of rows, which the per-step and per-panel kernels
-// stream, are then one contiguous run of memory.
+// Layout of a sample's state: slabs of 32 columns, each holding only the rows it can ever
+// hold (slab_offset and sidx in ffs_kernels.cuh), about Nc^2 / 2 entries per sample.
 #include <type_traits>
 
 #include "ffs_arith.cuh"
@@ -39,8 +36,6 @@ namespace fermi {
 
 constexpr int NB = 32;           // panel width (== warp size: one lane per panel column)
 
-__device__ __forceinline__ int64_t state_stride(int64_t Nc) { return Nc * ((Nc + 31) & ~(int64_t)31); }
-__device__ __forceinline__ int64_t sidx(int64_t Nc, int64_t j, int64_t c) { return ((c >> 5) * Nc + j) * 32 + (c & 31); }
 constexpr int kStepWarps = 8;    // samples per CTA of the step kernel
 // Rows of the state whose loads a step-kernel warp issues together.  Small groups keep
 // the kernel at 64 registers, so that four 256-thread CTAs fit an SM and a 4096-sample
@@ -260,7 +255,7 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
   const int64_t k0 = (k / NB) * NB, k1 = min(k0 + NB, Nc);
   const int i = (int)(k - k0);
   // this panel's slab: element (j, k0 + l) at Wp[j * 32 + l]
-  A* Wp = (A*)t.W + (size_t)b * state_stride(Nc) + (size_t)(k0 >> 5) * Nc * 32;
+  A* Wp = (A*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(k0 >> 5);
   A* W0P = (A*)t.W0P + (size_t)b * Nc * NB;
   const int32_t* mrow = a.m + b * N;
   const A* urow = (const A*)a.Ust + (int64_t)x * N;  // U in the state type
@@ -381,12 +376,12 @@ __device__ __forceinline__ int mcmc_draw(const StepArgs& a, const BlockedArgs& t
   // -h: h_j = -W[j][k] (j < k), h_k = 1, with the update of step k-1 (pending in the
   // state, see step_update) applied to column k when k-1 is in the same panel
   const bool pend = (k & 31) != 0;
-  const A nk = pend ? W[sidx(Nc, k - 1, k)] : T::zero();
+  const A nk = pend ? W[sidx(k - 1, k)] : T::zero();
   for (int64_t j = lane; j <= k; j += 32) {
     A v = T::neg(T::one());
     if (j < k) {
-      v = W[sidx(Nc, j, k)];
-      if (pend && j < k - 1) v = T::fms(v, W[sidx(Nc, j, k - 1)], nk);
+      v = W[sidx(j, k)];
+      if (pend && j < k - 1) v = T::fms(v, W[sidx(j, k - 1)], nk);
     }
     hs[mrow[j]] = v;
   }
@@ -611,7 +606,7 @@ __device__ __forceinline__ void panel_body(const StepArgs& a, const BlockedArgs&
   const int64_t c = c0 + lane;
   const bool cval = c < Nc;
   // slab of the columns [c0, c0 + 32) (c0 is a multiple of 32): element (j, c0 + cc) at Wc[j * 32 + cc]
-  A* Wc = (A*)t.W + (size_t)b * state_stride(Nc) + (size_t)(c0 >> 5) * Nc * 32;
+  A* Wc = (A*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c0 >> 5);
   const A* W0P = (const A*)t.W0P + (size_t)b * Nc * NB;
   const int32_t* mrow = a.m + b * N;
   const A* Us = (const A*)a.Ust;  // U in the state type
@@ -899,7 +894,7 @@ __global__ void column_operand_kernel(StepArgs a, BlockedArgs t, int64_t k1, int
   const A* W = (const A*)t.W + (size_t)b * state_stride(Nc);
   const int32_t* mrow = a.m + b * a.N;
   for (int64_t j = threadIdx.x; j <= k1; j += blockDim.x) {
-    const A v = (j < k1) ? T::neg(W[sidx(Nc, j, k1)]) : T::one();
+    const A v = (j < k1) ? T::neg(W[sidx(j, k1)]) : T::one();
     put_state<A>(a, op_mode, b, operand_col(a, mrow, j), v);
   }
 }

@@ -46,9 +46,9 @@ def test_l2_policy():
     flushed = {k for k, s in bench.WORKLOADS.items()
                if bench.working_set_bytes(s["L"], s["N"], s["B"], s["cplx"], "df64") < 2 * bench.L2_BYTES}
     assert flushed == {"chain64_N8_B10000"}
-    # the 64x64 lattice: 4096 samples x 1024 x 1024 complex double-float entries
+    # the 64x64 lattice: 4096 samples x 32 slabs x 32 (s + 1) rows x 32 complex double-floats
     s = bench.WORKLOADS["lattice64x64_N1024_B4096"]
-    assert bench.working_set_bytes(s["L"], s["N"], s["B"], s["cplx"], "df64") > 4096 * 1024 * 1024 * 16
+    assert bench.working_set_bytes(s["L"], s["N"], s["B"], s["cplx"], "df64") > 4096 * 512 * 32 * 33 * 16
 
 
 def test_reference_arm_under_torchrun_prints_one_line():
