@@ -27,6 +27,7 @@
 // per 32-lane quarter of tensor memory, each for 8 of the 32 columns), and the operand of
 // the next step from the updated column.
 #include <cfloat>
+#include <type_traits>
 
 #include "ffs_arith.cuh"
 #include "ffs_kernels.cuh"
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
   const int64_t b = blockIdx.y;
   const int64_t mt = blockIdx.x;
   if (a.nlen && a.nlen[b] <= k1) return;  // uniform over the CTA
+  using E = typename std::conditional<CX, cdf, df>::type;  // the state's element type
   const int64_t Nc = t.Nc;
   const int n_tiles = (int)((Nc - k1 + NT - 1) / NT);
   const uint32_t raw = smem_u32(smem_raw);
@@ -228,8 +230,17 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
     mbar_arrive_expect_tx(a_full, kABytes);
     for (int i = 0; i < kSlices; ++i)
       tma_load_2d(sA + i * kATile, &tmA, a_full, 0, (int32_t)((b * kSlices + i) * z.KP + mt * MT));
+    const E* Wb = (const E*)t.W + (size_t)b * state_stride(Nc);
+    const int64_t r_rows = min((int64_t)MT, k0 - mt * MT);
+    auto prefetch_slab = [&](int ntp) {  // the epilogue's old rows of slab ntp into L2
+      if (ntp < n_tiles && r_rows > 0)
+        prefetch_l2_bulk(Wb + slab_offset(((k1 >> 5) + ntp)) + mt * MT * 32, (uint32_t)(r_rows * 32 * sizeof(E)));
+    };
+    prefetch_slab(0);
+    prefetch_slab(1);
     int issued = 0;
     for (int nt = 0; nt < n_tiles; ++nt) {
+      prefetch_slab(nt + 2);
       const int s = nt % kBStages;
       if (nt >= kBStages && !mbar_wait(b_empty(s), ((nt / kBStages) - 1) & 1, abort_flag)) {
         *abort_flag = 1;
@@ -338,20 +349,27 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
       named_sync(quarter_bar, quarter_threads);     // all the quarter's columns are staged
       const size_t slab = (size_t)b * state_stride(Nc) + (size_t)slab_offset(c0 >> 5);
       const bool col_ok = ok && c0 + lane < Nc;
+      // all the warp's rows are loaded before any is stored, so that their loads overlap
+      E wv[kEpiCols];
+      E* Wc = (E*)t.W + slab;
 #pragma unroll
-      for (int rr = kEpiCols * h; rr < kEpiCols * h + kEpiCols; ++rr) {
+      for (int n = 0; n < kEpiCols; ++n) {
+        const int64_t jr = mt * MT + 32 * q + kEpiCols * h + n;
+        if (jr < k0 && col_ok) wv[n] = Wc[jr * 32 + lane];
+      }
+#pragma unroll
+      for (int n = 0; n < kEpiCols; ++n) {
+        const int rr = kEpiCols * h + n;
         const int64_t jr = mt * MT + 32 * q + rr;
         if (jr < k0 && col_ok) {
           const cdf p = *(const cdf*)(Pq + rr * kPRow + lane * 16);
           if constexpr (CX) {
-            cdf* Wc = (cdf*)t.W + slab;
-            cdf w = Wc[jr * 32 + lane];
+            cdf w = wv[n];
             w.re = df_sub(w.re, p.re);
             w.im = df_sub(w.im, p.im);
             Wc[jr * 32 + lane] = w;
           } else {
-            df* Wc = (df*)t.W + slab;
-            Wc[jr * 32 + lane] = df_sub(Wc[jr * 32 + lane], p.re);
+            Wc[jr * 32 + lane] = df_sub(wv[n], p.re);
           }
         }
       }
@@ -495,6 +513,10 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_real_kernel(const __grid_c
     for (int p = 0; p < kPairA; ++p)
       tma_load_2d(sA + p * kATile, &tmA, a_full, 0, (int32_t)((b * kPairA + p) * z.KP + mt * MT));
     const int64_t nslab = z.TP / NT;
+    const df* Wb = (const df*)t.W + (size_t)b * state_stride(Nc);
+    const int64_t r_rows = min((int64_t)MT, k0 - mt * MT);
+    for (int nt = 0; nt < 2 && nt < n_tiles; ++nt)
+      prefetch_l2_bulk(Wb + slab_offset(((k1 >> 5) + nt)) + mt * MT * 32, (uint32_t)(r_rows * 32 * sizeof(df)));
     int issued = 0;
     for (int nt = 0; nt < n_tiles; ++nt) {
       const int s = nt % kRBStages;
@@ -505,6 +527,9 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_real_kernel(const __grid_c
       mbar_arrive_expect_tx(b_full(s), kRBStage);
       tma_load_2d(sB + s * kRBStage, &tmB, b_full(s), 0, (int32_t)((b * nslab + nt) * kPairB * NT));
       ++issued;
+      // the epilogue's old rows of slab nt + 2 (128 rows x 256 bytes, contiguous) into L2
+      if (nt + 2 < n_tiles && r_rows > 0)
+        prefetch_l2_bulk(Wb + slab_offset(((k1 >> 5) + nt + 2)) + mt * MT * 32, (uint32_t)(r_rows * 32 * sizeof(df)));
     }
     mbar_drain(a_full, 0, kSpinLimit);
     for (int nt = (issued > kRBStages ? issued - kRBStages : 0); nt < issued; ++nt)
@@ -584,10 +609,18 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_real_kernel(const __grid_c
       named_sync(quarter_bar, quarter_threads);  // all the quarter's columns are staged
       df* Wc = (df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c0 >> 5);
       const bool col_ok = ok && c0 + lane < Nc;
+      // all the warp's rows are loaded before any is stored, so that their loads overlap
+      df wv[kEpiCols];
 #pragma unroll
-      for (int rr = kEpiCols * h; rr < kEpiCols * h + kEpiCols; ++rr) {
+      for (int n = 0; n < kEpiCols; ++n) {
+        const int64_t jr = mt * MT + 32 * q + kEpiCols * h + n;
+        wv[n] = (jr < k0 && col_ok) ? Wc[jr * 32 + lane] : df{0.f, 0.f};
+      }
+#pragma unroll
+      for (int n = 0; n < kEpiCols; ++n) {
+        const int rr = kEpiCols * h + n;
         const int64_t jr = mt * MT + 32 * q + rr;
-        if (jr < k0 && col_ok) Wc[jr * 32 + lane] = df_sub(Wc[jr * 32 + lane], *(const df*)(Pq + rr * kRPRow + lane * 8));
+        if (jr < k0 && col_ok) Wc[jr * 32 + lane] = df_sub(wv[n], *(const df*)(Pq + rr * kRPRow + lane * 8));
       }
       named_sync(quarter_bar, quarter_threads);  // before the next slab overwrites the staging rows
     }

@@ -275,7 +275,21 @@ __global__ void __launch_bounds__(kYThreads, 1)
     const int64_t c = c0 + cl;
     const bool cval = c < Nc;
     const df* Wc = (const df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
+    // one thread keeps the next two chunks of the CTA's four slabs (64 rows x 256 bytes
+    // each, contiguous) on their way into L2 while the current chunk is sliced
+    const df* Wb = (const df*)t.W + (size_t)b * state_stride(Nc);
+    auto prefetch_chunk = [&](int tcp) {
+      if (pid != 0 || tcp >= nch) return;
+      const int64_t r0 = (int64_t)tcp * YKC, rn = min((int64_t)YKC, k0 - r0);
+      for (int sl = 0; sl < YM / 32; ++sl) {
+        const int64_t cs = c0 + 32 * sl;
+        if (cs < Nc) prefetch_l2_bulk(Wb + slab_offset(cs >> 5) + r0 * 32, (uint32_t)(rn * 32 * sizeof(df)));
+      }
+    };
+    prefetch_chunk(0);
+    prefetch_chunk(1);
     for (int tc = 0; tc < nch; ++tc) {
+      prefetch_chunk(tc + 2);
       float th[32], tl[32];
       float mx = 0.f;
       const int64_t j0 = (int64_t)tc * YKC + 32 * q;

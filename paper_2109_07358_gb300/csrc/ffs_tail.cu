@@ -31,6 +31,7 @@
 #include "ffs_draw.cuh"
 #include "ffs_group.cuh"
 #include "ffs_kernels.cuh"
+#include "ffs_sm100.cuh"
 
 namespace fermi {
 
@@ -167,6 +168,30 @@ __device__ __forceinline__ int chunk_find(const float* __restrict__ p, int64_t L
   return (int)(ch * 128 + 4 * src + qs);
 }
 
+// The same chunk sum in two parts, so that the loads of several chunks can be issued
+// before any of their warp reductions: lane's four weights, then (v0 + v1) + (v2 + v3)
+// reduced over the warp in the order chunk_sum uses.
+__device__ __forceinline__ float4 chunk_load(const float* __restrict__ p, int64_t L, int64_t ch, int lane) {
+  const int64_t y0 = ch * 128 + 4 * lane;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (y0 + 3 < L) {
+    v = *(const float4*)(p + y0);
+  } else {
+    if (y0 < L) v.x = p[y0];
+    if (y0 + 1 < L) v.y = p[y0 + 1];
+    if (y0 + 2 < L) v.z = p[y0 + 2];
+  }
+  return v;
+}
+__device__ __forceinline__ double chunk_reduce(float4 v) {
+  float s = (v.x + v.y) + (v.z + v.w);
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return (double)s;
+}
+// Chunk sums of the normaliser pass kept in shared memory for the search pass: up to
+// kCsMax chunks per warp, i.e. L <= 16384; longer rows take the two-pass form.
+constexpr int kCsMax = 128;
+
 __device__ __forceinline__ int last_nonzero(const float* __restrict__ p, int64_t L, int lane) {
   int last = -1;
   for (int64_t y = lane; y < L; y += 32)
@@ -182,7 +207,7 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
 // ------------------------------------------------------------------ per-step body (one warp)
 template <typename A>
 __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& t, int64_t b, int64_t k,
-                                          int op_mode) {
+                                          int op_mode, double* csm) {
   using T = Ar<A>;
   const int lane = threadIdx.x & 31;
   const int64_t L = a.L, N = a.N, Nc = t.Nc;
@@ -197,10 +222,30 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
     return;
   }
 
-  // draw: Z over 128-site chunks, then the first chunk whose running sum passes t
+  // draw: Z over 128-site chunks, then the first chunk whose running sum passes t (both
+  // sums in chunk order; with the chunk sums cached, the search reads only the chosen chunk)
   const int64_t nch = (L + 127) / 128;
+  const bool cached = nch <= kCsMax;
   double Z = 0.0;
-  for (int64_t ch = 0; ch < nch; ++ch) Z += chunk_sum(prow, L, ch, lane);
+  if (cached) {
+    for (int64_t ch0 = 0; ch0 < nch; ch0 += 4) {  // four chunks' loads in flight together
+      float4 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        v[q] = (ch0 + q < nch) ? chunk_load(prow, L, ch0 + q, lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (ch0 + q < nch) {
+          const double sq = chunk_reduce(v[q]);
+          Z += sq;
+          if (lane == 0) csm[ch0 + q] = sq;
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    for (int64_t ch = 0; ch < nch; ++ch) Z += chunk_sum(prow, L, ch, lane);
+  }
   int x;
   const int f = forced_site(a, b, k);
   if (f != -1) {
@@ -210,10 +255,18 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
     const double tt = site_uniform(a.seed, a.first + (uint64_t)b, (int)k) * Z;
     x = -1;
     double base = 0.0;
-    for (int64_t ch = 0; ch < nch && x < 0; ++ch) {
-      const double cs = chunk_sum(prow, L, ch, lane);
-      if (base + cs > tt) x = chunk_find(prow, L, ch, lane, base, tt);
-      base += cs;
+    if (cached) {
+      for (int64_t ch = 0; ch < nch && x < 0; ++ch) {
+        const double cs = csm[ch];
+        if (base + cs > tt) x = chunk_find(prow, L, ch, lane, base, tt);
+        base += cs;
+      }
+    } else {
+      for (int64_t ch = 0; ch < nch && x < 0; ++ch) {
+        const double cs = chunk_sum(prow, L, ch, lane);
+        if (base + cs > tt) x = chunk_find(prow, L, ch, lane, base, tt);
+        base += cs;
+      }
     }
     if (x < 0) x = last_nonzero(prow, L, lane);
     if (x < 0) {
@@ -272,15 +325,29 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
   // together; two accumulation chains)
   constexpr int G = kStepRowGroup;
   A acc = T::zero(), acc2 = T::zero();
+  // rows stream from DRAM: keep the next 32-row groups on their way into L2 (one bulk
+  // prefetch per group, two groups ahead of the loads)
+  auto prefetch_rows = [&](int64_t j) {
+    if (lane == 0 && j < k) sm100::prefetch_l2_bulk(Wp + j * 32, (uint32_t)(min((int64_t)32, k - j) * 32 * sizeof(A)));
+  };
+  prefetch_rows(0);
+  prefetch_rows(32);
   for (int64_t j0 = 0; j0 < k; j0 += 32) {
+    prefetch_rows(j0 + 64);
     const int64_t jl = j0 + lane;
     const A uj = (jl < k) ? urow[mrow[jl]] : T::zero();
     const int jn = (int)min((int64_t)32, k - j0);
     int jj = 0;
-    for (; jj + G <= jn; jj += G) {
-      A wv[G];
+    // one group of lookahead: the next group's loads are issued before this group's
+    // stores (the compiler cannot move them across the stores on its own)
+    A wv[G];
 #pragma unroll
-      for (int q = 0; q < G; ++q) wv[q] = need ? Wp[(j0 + jj + q) * 32 + lane] : T::zero();
+    for (int q = 0; q < G; ++q) wv[q] = (need && G <= jn) ? Wp[(j0 + q) * 32 + lane] : T::zero();
+    for (; jj + G <= jn; jj += G) {
+      A wnx[G];
+      const bool more = jj + 2 * G <= jn;
+#pragma unroll
+      for (int q = 0; q < G; ++q) wnx[q] = (need && more) ? Wp[(j0 + jj + G + q) * 32 + lane] : T::zero();
       if (keep && live) {
 #pragma unroll
         for (int q = 0; q < G; ++q) W0P[(j0 + jj + q) * NB + lane] = wv[q];
@@ -300,6 +367,8 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
         acc = T::fms(acc, shfl_idx_any(uj, jj + q), gem ? wv[q] : T::zero());
         acc2 = T::fms(acc2, shfl_idx_any(uj, jj + q + 1), gem ? wv[q + 1] : T::zero());
       }
+#pragma unroll
+      for (int q = 0; q < G; ++q) wv[q] = wnx[q];
     }
     for (; jj < jn; ++jj) {
       const int64_t j = j0 + jj;
@@ -347,9 +416,10 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
 
 template <typename A>
 __global__ void __launch_bounds__(256, 4) tail_step_kernel(StepArgs a, BlockedArgs t, int64_t k, int op_mode) {
+  __shared__ double csm[kStepWarps][kCsMax];
   const int64_t b = (int64_t)blockIdx.x * kStepWarps + (threadIdx.x >> 5);
   if (b >= a.bw) return;
-  step_warp<A>(a, t, b, k, op_mode);
+  step_warp<A>(a, t, b, k, op_mode, csm[threadIdx.x >> 5]);
 }
 
 // ------------------------------------------------------------------ large-L draw (Section S-7)
@@ -803,6 +873,7 @@ static size_t panel_smem(size_t es) {
 template <typename A>
 __global__ void __launch_bounds__(256, 4)
     step_group_kernel(const GroupInst* __restrict__ inst, const GroupEntry* __restrict__ ent, int n, int op_mode) {
+  __shared__ double csm[kStepWarps][kCsMax];
   const int64_t item = blockIdx.x;
   const int e = group_find(ent, n, item);
   const GroupInst* gi = inst + ent[e].inst;
@@ -810,7 +881,7 @@ __global__ void __launch_bounds__(256, 4)
   const BlockedArgs t = gi->t;
   const int64_t b = (item - ent[e].start) * kStepWarps + (threadIdx.x >> 5);
   if (b >= a.bw) return;
-  step_warp<A>(a, t, b, ent[e].k, op_mode);
+  step_warp<A>(a, t, b, ent[e].k, op_mode, csm[threadIdx.x >> 5]);
 }
 
 template <typename A>
