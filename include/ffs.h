@@ -371,7 +371,8 @@ int ffs_jastrow_estimate(const int32_t* x, int64_t B, int64_t n_occ, int64_t n_o
  * tensor-core residual launch of h (the paper has no counterpart: this exercises the
  * library's bounded waits).  FFS_FAULT_SKIP_ARRIVAL: the TMA producer of that launch's
  * first CTA skips its first pipeline stage (no arrival, no copy) and every wait of the
- * launch gives up after 4096 polls instead of about 4 million, so the MMA issuer's wait
+ * launch gives up after 4096 polls instead of 262144 (a poll suspends the waiting thread
+ * for at most 100 microseconds), so the MMA issuer's wait
  * runs out, the launch records FFS_E_TIMEOUT in the status word (ffs_sync returns it)
  * and every role of the CTA leaves without a copy in flight and with its tensor memory
  * freed.  The samples of that call are invalid; the handle stays usable and its next

@@ -14,7 +14,7 @@ struct TcArgs {
   float* P;
   const uint32_t* mask;
   int* status;
-  uint32_t spin = 1u << 22;  // polls before a wait gives up (FFS_E_TIMEOUT)
+  uint32_t spin = 1u << 18;  // polls before a wait gives up (FFS_E_TIMEOUT); each may suspend 100 us
   int fault = 0;             // failure-path test: the first CTA's producer skips stage 0
 };
 

@@ -9,9 +9,12 @@
 namespace fermi {
 namespace sm100 {
 
-// Iteration cap of every spin-wait (each try_wait may also suspend briefly), so a
-// wait that can never complete returns instead of hanging the GPU.
-constexpr uint32_t kSpinLimit = 1u << 22;
+// Waits suspend the waiting thread (try_wait with a suspend-time hint) until the phase
+// completes or kSuspendNs pass, so that waiting warps do not take issue slots from the
+// warps they wait for.  kSpinLimit caps the polls, so a wait that can never complete
+// returns (after at most kSpinLimit x kSuspendNs, about 26 s) instead of hanging the GPU.
+constexpr uint32_t kSuspendNs = 100000;
+constexpr uint32_t kSpinLimit = 1u << 18;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -34,10 +37,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
