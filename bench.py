@@ -148,6 +148,32 @@ def blocked_flops_per_sample(N, cplx, nb=32):
     return {"step": step * f, "panel_s": panel_s * f, "panel": panel * f, "top": top * f}
 
 
+def blocked_bytes_per_sample(L, N, e, nb=32):
+    """Algorithmic HBM bytes per sample of the memory-bound kernels of the blocked state
+    update (e = bytes per state entry: 8 for real double-float or FP64, 16 for complex):
+      step  per step k: the L FP32 weights read by the draw; the live panel block read
+            (k x (k1 - k) entries) and written back (k x (k1 - k - 1)); at the first step
+            of a panel the k0 x nb copy W0_P written;
+      new   per panel, T = [k1, N): W0_T read (k0 x |T|), the new rows' U entries read and
+            the new rows written (2 x nb x |T|);
+      top   per panel: W0_T read and Top written (2 x k0 x |T|), W0_P read (k0 x nb)."""
+    step = new = top = 0.0
+    for k in range(N):
+        k0 = (k // nb) * nb
+        k1 = min(k0 + nb, N)
+        step += 4.0 * L
+        if k + 1 < N:
+            step += e * (k * (k1 - k) + k * (k1 - k - 1) + (k0 * nb if k == k0 else 0))
+    for k0 in range(0, N, nb):
+        k1 = min(k0 + nb, N)
+        if k1 >= N:
+            break
+        T = N - k1
+        new += e * (k0 * T + 2 * nb * T)
+        top += e * (2 * k0 * T + k0 * nb)
+    return {"step": step, "new": new, "top": top}
+
+
 # Instruction counts behind the derived CUDA-core peaks of the double-float state kernels:
 # a real lazy multiply-add (lz_mac) is 13 FP32-pipe instructions for 2 flops; a complex
 # one by Karatsuba is three of them (39 instructions) for 8 flops.
@@ -630,21 +656,53 @@ def phase_report(prof, L, N, B, K, cplx, chosen, state, peaks, trailing_tc):
             "traffic": None, "peak_source": res_src + " (measured; the kernel runs inside a long step)",
             "algorithmic": "the paper's 2Lk flops per sample-step, L N (N+1) per sample" + (" x4 complex" if cplx else ""),
             "per_launch": "algorithmic flops of all residual launches / their summed CUDA-event time"}
+    e = {"df64": 8, "fp64": 8, "fp32": 4}[state] * (2 if cplx else 1)
+    bb = {k: v * B * K for k, v in blocked_bytes_per_sample(L, N, e).items()}
+
+    def gbs(by, ms):
+        return by / (ms / 1e3) / 1e9 if ms else None
+
+    # with the tensor-core trailing update both halves of the panel end run on tcgen05:
+    # the new rows (FFS_PHASE_PANEL: C's slices + ozy_kernel) and Top (FFS_PHASE_PANEL_TC)
+    new_tc = bool(ptc_n) and trailing_tc
     phases = {
         "residual": {"kernel": roof["kernel"], "ms": res_ms / K, "launches_per_step": res_n / K,
                      "algorithmic_tflops": ach, "issued_tflops": tfl(issued * mult, res_ms)},
         "tail_step": {"kernel": "tail_step_kernel", "ms": tail_ms / K, "launches_per_step": tail_n / K,
-                      "algorithmic_tflops": tfl(bf["step"], tail_ms)},
+                      "algorithmic_tflops": tfl(bf["step"], tail_ms), "algorithmic_gbs": gbs(bb["step"], tail_ms)},
         "tail_panel_s": {"kernel": "tail_panel_s_kernel", "ms": pans_ms / K, "launches_per_step": pans_n / K,
                          "algorithmic_tflops": tfl(bf["panel_s"], pans_ms)},
-        "tail_panel": {"kernel": "tail_panel_kernel", "ms": panel_ms / K, "launches_per_step": panel_n / K,
-                       "algorithmic_tflops": tfl(bf["panel"] - (bf["top"] if ptc_n else 0.0), panel_ms)},
+        "tail_panel": {"kernel": "ozy_kernel (+ C slices)" if new_tc else "tail_panel_kernel",
+                       "ms": panel_ms / K, "launches_per_step": panel_n / K,
+                       "algorithmic_tflops": tfl(bf["panel"] - (bf["top"] if ptc_n else 0.0), panel_ms),
+                       **({"algorithmic_gbs": gbs(bb["new"], panel_ms)} if new_tc else {})},
         "perm": {"kernel": "perm_init_kernel", "ms": perm_ms / K, "launches_per_step": perm_n / K},
     }
     if ptc_n:
         phases["tail_panel_tc"] = {"kernel": "oz_top_kernel (+ slices, operand)", "ms": ptc_ms / K,
-                                   "launches_per_step": ptc_n / K, "algorithmic_tflops": tfl(bf["top"], ptc_ms)}
-    # the state update's largest CUDA-core kernel against the peak of its own arithmetic
+                                   "launches_per_step": ptc_n / K, "algorithmic_tflops": tfl(bf["top"], ptc_ms),
+                                   "algorithmic_gbs": gbs(bb["top"], ptc_ms)}
+    total_ms = max(1e-9, res_ms + tail_ms + panel_ms + pans_ms + ptc_ms + perm_ms)
+    # the state update's dominant phase: a memory-bound one (the per-step update, or the
+    # tensor-core panel-end halves, whose issued BF16 products per state byte sit below the
+    # tensor ridge) against the measured HBM copy rate; the CUDA-core new-row kernel
+    # against the derived peak of its own arithmetic
+    cands = {"tail_step": tail_ms, "tail_panel": panel_ms}
+    if ptc_n:
+        cands["tail_panel_tc"] = ptc_ms
+    dom = max(cands, key=cands.get)
+    if dom != "tail_panel" or new_tc:
+        by = {"tail_step": bb["step"], "tail_panel": bb["new"], "tail_panel_tc": bb["top"]}[dom]
+        a_gbs = gbs(by, cands[dom])
+        roof_tail = {"kernel": phases[dom]["kernel"], "phase": dom, "bound": "hbm", "achieved": a_gbs,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": a_gbs / peaks["hbm_gbs"] if a_gbs else None, "traffic": None,
+                     "peak_source": f"{peaks['source']} hbm_gbs (copy bandwidth)",
+                     "algorithmic": blocked_bytes_per_sample.__doc__.split("\n")[0].strip() + f" (e = {e} bytes)",
+                     "share_of_step": cands[dom] / total_ms}
+        launches = int(res_n + tail_n + panel_n + pans_n + ptc_n + perm_n) // K
+        return phases, roof, roof_tail, launches
+    # the CUDA-core new-row kernel against the peak of its own arithmetic
     if state == "df64":
         instr = DF_INSTR_COMPLEX if cplx else DF_INSTR_REAL
         st_peak = FP32_INSTR_PER_S / instr * (8 if cplx else 2) / 1e12
@@ -657,10 +715,10 @@ def phase_report(prof, L, N, B, K, cplx, chosen, state, peaks, trailing_tc):
         st_peak, st_src = NOMINAL_FP32_TFLOPS, "nominal FP32 rate (152 SMs x 128 lanes x 2 x 2.07 GHz)"
     fl_panel = bf["panel"] - (bf["top"] if ptc_n else 0.0)
     tail_ach = tfl(fl_panel, panel_ms)
-    roof_tail = {"kernel": f"tail_panel_kernel ({state} state)", "bound": "alu", "achieved": tail_ach,
-                 "peak": st_peak, "unit": "TFLOP/s", "frac": tail_ach / st_peak if tail_ach else None,
-                 "traffic": None, "peak_source": st_src,
-                 "share_of_step": panel_ms / max(1e-9, res_ms + tail_ms + panel_ms + pans_ms + ptc_ms + perm_ms)}
+    roof_tail = {"kernel": f"tail_panel_kernel ({state} state)", "phase": "tail_panel", "bound": "alu",
+                 "achieved": tail_ach, "peak": st_peak, "unit": "TFLOP/s",
+                 "frac": tail_ach / st_peak if tail_ach else None,
+                 "traffic": None, "peak_source": st_src, "share_of_step": panel_ms / total_ms}
     launches = int(res_n + tail_n + panel_n + pans_n + ptc_n + perm_n) // K
     return phases, roof, roof_tail, launches
 

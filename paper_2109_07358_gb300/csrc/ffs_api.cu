@@ -411,7 +411,7 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
   const bool plain = op == kOpNone;
   const bool grouped = grouped_form(h);
   const bool tc_top = (h->flags & FFS_TRAILING_TC) && blocked(h);
-  const bool tc_new = tc_top && !h->cplx;  // the new rows (Y, Bot) on the tensor cores too
+  const bool tc_new = tc_top;  // the new rows (Y, Bot) on the tensor cores too
   const int64_t G = FFS_GROUP_SIZE;
   if (grouped && (first_sample_index % G) != 0)
     return fail(h, FFS_E_ARG, "grouped form: first_sample_index must be a multiple of 128");
@@ -431,7 +431,7 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
   if (out_probs && !probs_dev) per += (size_t)ldx * h->L * 4;
   if (grouped) per += group_copy_bytes(h) / G + 1;  // a group's operand copy, shared by its 128 samples
   if (tc_top) per += oz_bytes_per_sample(n_steps);   // slices of the tensor-core trailing update
-  if (tc_new) per += ozy_bytes_per_sample(n_steps);  // C's slices of the tensor-core new rows
+  if (tc_new) per += ozy_bytes_per_sample(n_steps, h->cplx);  // C's slices of the tensor-core new rows
   size_t free_b = 0, total_b = 0;
   FFS_CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t reserve = (size_t)512 << 20;

@@ -92,11 +92,11 @@ cudaError_t launch_oz_top(ffs_ctx* c, const StepArgs& a, const BlockedArgs& t, i
 cudaError_t oz_prepare(ffs_ctx* c, int64_t Bw, int64_t Nc);
 size_t oz_bytes_per_sample(int64_t Nc);
 cudaError_t configure_oz();
-// Tensor-core new rows (ffs_ozaki_y.cu, real state): C's slices, then Y = U - C W0_T and
-// Bot = S^-1 Y written as the panel's rows of the trailing columns.
+// Tensor-core new rows (ffs_ozaki_y.cu, double-float state): C's slices, then
+// Y = U - C W0_T and Bot = S^-1 Y written as the panel's rows of the trailing columns.
 cudaError_t launch_oz_y(ffs_ctx* c, const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, cudaStream_t s);
 cudaError_t ozy_prepare(ffs_ctx* c, int64_t Bw, int64_t Nc);
-size_t ozy_bytes_per_sample(int64_t Nc);
+size_t ozy_bytes_per_sample(int64_t Nc, bool cplx);
 cudaError_t configure_oz_y();
 
 // Large-L draw of Section S-7: a Metropolis chain of m_cond updates per step, then the

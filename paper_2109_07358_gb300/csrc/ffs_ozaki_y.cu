@@ -1,4 +1,4 @@
-// New rows of the trailing update on tensor cores (FFS_TRAILING_TC, real double-float state).
+// New rows of the trailing update on tensor cores (FFS_TRAILING_TC, double-float state).
 //
 // At a panel end (panel rows k0..k1-1, trailing columns T = [k1, Nc)) the new rows of the
 // blocked state are (Supplementary Section S-1's elimination, in panels)
@@ -27,6 +27,8 @@
 // the swizzled shared-memory operand tiles (two threads per trailing column, 32 old rows
 // each), warps 10-17 drain the accumulators (two per tensor-memory lane quarter, 16 new
 // rows each), then form Bot = S^-1 Y and write the new rows.
+#include <type_traits>
+
 #include "ffs_arith.cuh"
 #include "ffs_kernels.cuh"
 #include "ffs_residual_tc.cuh"
@@ -55,7 +57,7 @@ constexpr uint32_t kYAccCols = 256;         // one accumulator set: 7 groups x 3
 constexpr uint32_t kYTmemCols = 512;        // two sets
 constexpr uint32_t kYSigRing = 4;           // chunks of column scales kept for the epilogue
 constexpr uint32_t kYSmem = kYAHalves * kYAHalf + kYBStages * kYBStage + kYSigRing * YM * 4 + 1024 + 256;
-static_assert(YN * YM * 8 + YN * YN * 8 <= kYAHalves * kYAHalf, "Y and S^-1 staging fit the operand ring");
+static_assert(YN * YM * 8 + YN * YN * 16 <= kYAHalves * kYAHalf, "Y and S^-1 staging fit the operand ring");
 constexpr uint32_t kYIdesc = idesc_bf16(YM, YN);
 
 // Power-of-two scale sigma > max (as sigma, 1/sigma); 1 for an all-zero chunk.  A
@@ -103,7 +105,10 @@ __device__ __forceinline__ uint32_t sw128_chunk(uint32_t r, uint32_t kc) {
 
 // C's slices for one sample, panel and K chunk: rows i < 32 of C = U[x_new, m_<k0]
 // (Ust in double-float), layout [b][chunk][slice][32 rows][64] BF16 with the row scales
-// in [b][chunk][32].  One warp per (row, chunk, sample); lane l takes columns 2l, 2l+1.
+// in [b][chunk][32].  One warp per (row, chunk, sample).  Real: a chunk is 64 old rows,
+// lane l takes columns 2l, 2l+1.  Complex: a chunk is 32 old rows as 64 interleaved
+// K elements (Re C, Im C); lane l takes old row l of the chunk.
+template <bool CX>
 __global__ void __launch_bounds__(256) ozc_slice_kernel(StepArgs a, BlockedArgs t, OzYArgs z, int64_t k0,
                                                         int64_t k1) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -114,15 +119,21 @@ __global__ void __launch_bounds__(256) ozc_slice_kernel(StepArgs a, BlockedArgs 
   if (a.nlen && a.nlen[b] <= k1) return;
   const int32_t* mrow = a.m + b * a.N;
   const int xi = a.x[b * a.ldx + k0 + i];
-  const df* urow = (const df*)a.Ust + (int64_t)xi * a.N;
   df v[2];
-  float mx = 0.f;
+  if constexpr (CX) {
+    const int64_t j = tc * (YKC / 2) + lane;
+    const cdf u = (j < k0) ? ((const cdf*)a.Ust)[(int64_t)xi * a.N + mrow[j]] : cdf{df{0.f, 0.f}, df{0.f, 0.f}};
+    v[0] = u.re;
+    v[1] = u.im;
+  } else {
+    const df* urow = (const df*)a.Ust + (int64_t)xi * a.N;
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int64_t j = tc * YKC + 2 * lane + q;
-    v[q] = (j < k0) ? urow[mrow[j]] : df{0.f, 0.f};
-    mx = fmaxf(mx, fabsf(v[q].hi));
+    for (int q = 0; q < 2; ++q) {
+      const int64_t j = tc * YKC + 2 * lane + q;
+      v[q] = (j < k0) ? urow[mrow[j]] : df{0.f, 0.f};
+    }
   }
+  float mx = fmaxf(fabsf(v[0].hi), fabsf(v[1].hi));
 #pragma unroll
   for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   float sigma, inv;
@@ -142,16 +153,24 @@ __global__ void __launch_bounds__(256) ozc_slice_kernel(StepArgs a, BlockedArgs 
   if (lane == 0) z.Cs[(b * z.n_chunks + tc) * YN + i] = sigma;
 }
 
-// Y, Bot and the new rows for 128 trailing columns of one sample (real double-float state).
+// Y, Bot and the new rows for one sample: 128 trailing columns of a real double-float
+// state, or 64 of a complex one.  A complex column c becomes two real operand rows over
+// K elements interleaved per old row j, (Re W, -Im W) and (Im W, Re W), so that against
+// the rows (Re C, Im C) of B they give Re and Im of (C W0_T)[i, c]; the MMAs, the tensor
+// memory and the pipeline are those of the real kernel.
+template <bool CX>
 __global__ void __launch_bounds__(kYThreads, 1)
     ozy_kernel(const __grid_constant__ CUtensorMap tmC, StepArgs a, BlockedArgs t, OzYArgs z, int64_t k0, int64_t k1) {
+  using E = typename std::conditional<CX, cdf, df>::type;  // the state's element type
+  constexpr int YCOL = CX ? YM / 2 : YM;                   // trailing columns per CTA
+  constexpr int JC = CX ? YKC / 2 : YKC;                   // old rows per K chunk
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t b = blockIdx.y;
   if (a.nlen && a.nlen[b] <= k1) return;  // uniform over the CTA
   const int64_t Nc = t.Nc;
-  const int64_t c0 = k1 + (int64_t)blockIdx.x * YM;
-  const int nch = (int)((k0 + YKC - 1) / YKC);
+  const int64_t c0 = k1 + (int64_t)blockIdx.x * YCOL;
+  const int nch = (int)((k0 + JC - 1) / JC);
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (sbase - raw);
@@ -268,22 +287,25 @@ __global__ void __launch_bounds__(kYThreads, 1)
       mbar_drain(mma_done, 0, kSpinLimit);
     }
   } else if (warp < 2 + kYProdWarps) {
-    // ---- producers: thread pair (2 r, 2 r + 1) owns trailing column c0 + r, old rows
+    // ---- producers: thread pair (2 r, 2 r + 1) owns operand row r (real: trailing column
+    // c0 + r; complex: column c0 + r / 2, its (Re, -Im) or (Im, Re) row), K elements
     // [32 q, 32 q + 32) of each chunk (q = the thread's parity)
     const int pid = threadIdx.x - 64;
-    const int cl = pid >> 1, q = pid & 1;
+    const int q = pid & 1, ar = pid >> 1;
+    const int cl = CX ? (ar >> 1) : ar;
+    const int rpart = CX ? (ar & 1) : 0;
     const int64_t c = c0 + cl;
     const bool cval = c < Nc;
-    const df* Wc = (const df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
-    // one thread keeps the next two chunks of the CTA's four slabs (64 rows x 256 bytes
-    // each, contiguous) on their way into L2 while the current chunk is sliced
-    const df* Wb = (const df*)t.W + (size_t)b * state_stride(Nc);
+    const E* Wc = (const E*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
+    // one thread keeps the next two chunks of the CTA's slabs (JC rows each, contiguous) on
+    // their way into L2 while the current chunk is sliced
+    const E* Wb = (const E*)t.W + (size_t)b * state_stride(Nc);
     auto prefetch_chunk = [&](int tcp) {
       if (pid != 0 || tcp >= nch) return;
-      const int64_t r0 = (int64_t)tcp * YKC, rn = min((int64_t)YKC, k0 - r0);
-      for (int sl = 0; sl < YM / 32; ++sl) {
+      const int64_t r0 = (int64_t)tcp * JC, rn = min((int64_t)JC, k0 - r0);
+      for (int sl = 0; sl < YCOL / 32; ++sl) {
         const int64_t cs = c0 + 32 * sl;
-        if (cs < Nc) prefetch_l2_bulk(Wb + slab_offset(cs >> 5) + r0 * 32, (uint32_t)(rn * 32 * sizeof(df)));
+        if (cs < Nc) prefetch_l2_bulk(Wb + slab_offset(cs >> 5) + r0 * 32, (uint32_t)(rn * 32 * sizeof(E)));
       }
     };
     prefetch_chunk(0);
@@ -292,15 +314,30 @@ __global__ void __launch_bounds__(kYThreads, 1)
       prefetch_chunk(tc + 2);
       float th[32], tl[32];
       float mx = 0.f;
-      const int64_t j0 = (int64_t)tc * YKC + 32 * q;
+      if constexpr (CX) {
+        const int64_t j0 = (int64_t)tc * JC + 16 * q;
 #pragma unroll
-      for (int e = 0; e < 32; ++e) {
-        const df v = (cval && j0 + e < k0) ? Wc[(j0 + e) * 32] : df{0.f, 0.f};
-        th[e] = v.hi;
-        tl[e] = v.lo;
-        mx = fmaxf(mx, fabsf(v.hi));
+        for (int e = 0; e < 16; ++e) {
+          const cdf v = (cval && j0 + e < k0) ? Wc[(j0 + e) * 32] : cdf{df{0.f, 0.f}, df{0.f, 0.f}};
+          const df x0 = rpart ? v.im : v.re, x1 = rpart ? v.re : df_neg(v.im);
+          th[2 * e] = x0.hi;
+          tl[2 * e] = x0.lo;
+          th[2 * e + 1] = x1.hi;
+          tl[2 * e + 1] = x1.lo;
+          mx = fmaxf(mx, fmaxf(fabsf(v.re.hi), fabsf(v.im.hi)));
+        }
+      } else {
+        const int64_t j0 = (int64_t)tc * JC + 32 * q;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          const df v = (cval && j0 + e < k0) ? Wc[(j0 + e) * 32] : df{0.f, 0.f};
+          th[e] = v.hi;
+          tl[e] = v.lo;
+          mx = fmaxf(mx, fabsf(v.hi));
+        }
       }
       mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      if constexpr (CX) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));  // both rows of the column
       float sigma, inv;
       ypow2(mx, sigma, inv);
       // x / sigma first, then 2^7: inv alone can be 2^125, so inv 2^7 would overflow
@@ -310,7 +347,7 @@ __global__ void __launch_bounds__(kYThreads, 1)
         tl[e] = __fmul_rn(__fmul_rn(tl[e], inv), 128.f);
       }
       const int rs = tc & (kYSigRing - 1);
-      if (q == 0) sSig[rs * YM + cl] = sigma;
+      if (q == 0) sSig[rs * YM + ar] = sigma;
       __syncwarp();
       if (lane == 0) mbar_arrive(sig_full(rs));
       bool ok = true;
@@ -332,7 +369,7 @@ __global__ void __launch_bounds__(kYThreads, 1)
               const float x1 = slice_step(th[8 * g + 2 * e + 1], tl[8 * g + 2 * e + 1]);
               w4[e] = pack_bf16x2(x0, x1);
             }
-            const uint32_t addr = stA + s * kYATile + sw128_chunk((uint32_t)cl, (uint32_t)(4 * q + g));
+            const uint32_t addr = stA + s * kYATile + sw128_chunk((uint32_t)ar, (uint32_t)(4 * q + g));
             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w4[0]), "r"(w4[1]), "r"(w4[2]),
                          "r"(w4[3])
                          : "memory");
@@ -353,7 +390,9 @@ __global__ void __launch_bounds__(kYThreads, 1)
     const int ew = warp - (2 + kYProdWarps);
     const int qd = warp & 3;                   // tensor-memory lane quarter of this warp
     const int hh = ew >> 2;                    // new rows [16 hh, 16 hh + 16)
-    const int cl = 32 * qd + lane;
+    const int ar = 32 * qd + lane;             // operand row = tensor-memory lane
+    const int cl = CX ? (ar >> 1) : ar;        // trailing column within the CTA
+    const int rpart = CX ? (ar & 1) : 0;       // complex: 0 = Re, 1 = Im of the product
     const int64_t c = c0 + cl;
     const bool cval = c < Nc;
     df yacc[16];
@@ -385,7 +424,7 @@ __global__ void __launch_bounds__(kYThreads, 1)
       }
       // the chunk's column scale is read before the accumulators are released: a producer
       // can overwrite its ring slot only after that release (four chunks later)
-      const float sc = sSig[rs * YM + cl] * 0x1p-14f;
+      const float sc = sSig[rs * YM + ar] * 0x1p-14f;
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty(u));
@@ -397,32 +436,68 @@ __global__ void __launch_bounds__(kYThreads, 1)
       }
     }
     // Y = U[x_new, m_c] - (C W0_T)[:, c], staged for Bot = S^-1 Y
-    df* Ys = (df*)gbase;                       // [32 new rows][128 columns]
-    df* Si = Ys + YN * YM;                     // [32][32]
     const int32_t* mrow = a.m + b * a.N;
     const int mc = cval ? mrow[c] : 0;
-#pragma unroll
-    for (int n = 0; n < 16; ++n) {
-      const int i = 16 * hh + n;
-      df y = df{0.f, 0.f};
-      if (cval) {
-        const int xi = a.x[b * a.ldx + k0 + i];
-        y = df_sub(((const df*)a.Ust)[(int64_t)xi * a.N + mc], yacc[n]);
-      }
-      Ys[i * YM + cl] = y;
-    }
     const int et = threadIdx.x - 32 * (2 + kYProdWarps);  // 0 .. 255
-    for (int e = et; e < YN * YN; e += 32 * kYEpiWarps) Si[e] = ((const df*)t.Sinv)[(size_t)b * YN * YN + e];
-    named_sync(1, 32 * kYEpiWarps);
-    if (cval) {
-      df* Wn = (df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
-#pragma unroll 1
+    if constexpr (CX) {
+      cdf* Ys = (cdf*)gbase;                   // [32 new rows][64 columns]
+      cdf* Si = Ys + YN * YCOL;                // [32][32]
+#pragma unroll
       for (int n = 0; n < 16; ++n) {
         const int i = 16 * hh + n;
-        lzf acc{0.f, 0.f};
+        df y = df{0.f, 0.f};
+        if (cval) {
+          const int xi = a.x[b * a.ldx + k0 + i];
+          const cdf d = ((const cdf*)a.Ust)[(int64_t)xi * a.N + mc];
+          y = df_sub(rpart ? d.im : d.re, yacc[n]);
+        }
+        ((df*)&Ys[i * YCOL + cl])[rpart] = y;
+      }
+      for (int e = et; e < YN * YN; e += 32 * kYEpiWarps) Si[e] = ((const cdf*)t.Sinv)[(size_t)b * YN * YN + e];
+      named_sync(1, 32 * kYEpiWarps);
+      if (cval) {
+        // this thread's 8 of the column's 32 new rows: Bot = S^-1 Y in four real products
+        cdf* Wn = (cdf*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
+#pragma unroll 1
+        for (int n = 0; n < 8; ++n) {
+          const int i = 16 * hh + 8 * rpart + n;
+          lzf re{0.f, 0.f}, im{0.f, 0.f};
+#pragma unroll 4
+          for (int ip = 0; ip < YN; ++ip) {
+            const cdf sv = Si[i * YN + ip], yv = Ys[ip * YCOL + cl];
+            lz_mac(re, sv.re, yv.re);
+            lz_mac(re, df_neg(sv.im), yv.im);
+            lz_mac(im, sv.re, yv.im);
+            lz_mac(im, sv.im, yv.re);
+          }
+          Wn[(k0 + i) * 32] = cdf{lz_get(re), lz_get(im)};
+        }
+      }
+    } else {
+      df* Ys = (df*)gbase;                     // [32 new rows][128 columns]
+      df* Si = Ys + YN * YM;                   // [32][32]
+#pragma unroll
+      for (int n = 0; n < 16; ++n) {
+        const int i = 16 * hh + n;
+        df y = df{0.f, 0.f};
+        if (cval) {
+          const int xi = a.x[b * a.ldx + k0 + i];
+          y = df_sub(((const df*)a.Ust)[(int64_t)xi * a.N + mc], yacc[n]);
+        }
+        Ys[i * YM + cl] = y;
+      }
+      for (int e = et; e < YN * YN; e += 32 * kYEpiWarps) Si[e] = ((const df*)t.Sinv)[(size_t)b * YN * YN + e];
+      named_sync(1, 32 * kYEpiWarps);
+      if (cval) {
+        df* Wn = (df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
+#pragma unroll 1
+        for (int n = 0; n < 16; ++n) {
+          const int i = 16 * hh + n;
+          lzf acc{0.f, 0.f};
 #pragma unroll 8
-        for (int ip = 0; ip < YN; ++ip) lz_mac(acc, Si[i * YN + ip], Ys[ip * YM + cl]);
-        Wn[(k0 + i) * 32] = lz_get(acc);
+          for (int ip = 0; ip < YN; ++ip) lz_mac(acc, Si[i * YN + ip], Ys[ip * YM + cl]);
+          Wn[(k0 + i) * 32] = lz_get(acc);
+        }
       }
     }
     (void)dead;
@@ -438,14 +513,17 @@ __global__ void __launch_bounds__(kYThreads, 1)
 
 }  // namespace
 
-size_t ozy_bytes_per_sample(int64_t Nc) {
-  const int64_t nch = (Nc + YKC - 1) / YKC;
+// Old rows per K chunk: 64 real or 32 complex (64 interleaved K elements).
+static int64_t ozy_chunk_rows(bool cplx) { return cplx ? YKC / 2 : YKC; }
+
+size_t ozy_bytes_per_sample(int64_t Nc, bool cplx) {
+  const int64_t nch = (Nc + ozy_chunk_rows(cplx) - 1) / ozy_chunk_rows(cplx);
   return (size_t)nch * kYS * YN * YKC * 2 + (size_t)nch * YN * 4;
 }
 
 cudaError_t ozy_prepare(ffs_ctx* c, int64_t Bw, int64_t Nc) {
-  const int64_t nch = (Nc + YKC - 1) / YKC;
-  const size_t need = (size_t)Bw * ozy_bytes_per_sample(Nc);
+  const int64_t nch = (Nc + ozy_chunk_rows(c->cplx) - 1) / ozy_chunk_rows(c->cplx);
+  const size_t need = (size_t)Bw * ozy_bytes_per_sample(Nc, c->cplx);
   if (need > c->ozy_bytes) {
     cudaFree(c->ozy_buf);
     c->ozy_buf = nullptr;
@@ -469,22 +547,33 @@ cudaError_t ozy_prepare(ffs_ctx* c, int64_t Bw, int64_t Nc) {
   return cudaSuccess;
 }
 
-cudaError_t launch_oz_y(ffs_ctx* c, const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, cudaStream_t s) {
-  if (k1 >= t.Nc || a.bw <= 0) return cudaSuccess;
-  if (a.cplx) return cudaErrorNotSupported;
+template <bool CX>
+static void ozy_launch(ffs_ctx* c, const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, cudaStream_t s) {
+  constexpr int64_t YCOL = CX ? YM / 2 : YM, JC = CX ? YKC / 2 : YKC;
   const OzYArgs z = c->ozy;
-  const int64_t nch = (k0 + YKC - 1) / YKC;
+  const int64_t nch = (k0 + JC - 1) / JC;
   if (nch > 0) {
     const dim3 gc((unsigned)(YN / 8), (unsigned)nch, (unsigned)a.bw);
-    ozc_slice_kernel<<<gc, 256, 0, s>>>(a, t, z, k0, k1);
+    ozc_slice_kernel<CX><<<gc, 256, 0, s>>>(a, t, z, k0, k1);
   }
-  const dim3 gy((unsigned)((t.Nc - k1 + YM - 1) / YM), (unsigned)a.bw);
-  ozy_kernel<<<gy, kYThreads, kYSmem, s>>>(c->ozyC, a, t, z, k0, k1);
+  const dim3 gy((unsigned)((t.Nc - k1 + YCOL - 1) / YCOL), (unsigned)a.bw);
+  ozy_kernel<CX><<<gy, kYThreads, kYSmem, s>>>(c->ozyC, a, t, z, k0, k1);
+}
+
+cudaError_t launch_oz_y(ffs_ctx* c, const StepArgs& a, const BlockedArgs& t, int64_t k0, int64_t k1, cudaStream_t s) {
+  if (k1 >= t.Nc || a.bw <= 0) return cudaSuccess;
+  if (a.cplx)
+    ozy_launch<true>(c, a, t, k0, k1, s);
+  else
+    ozy_launch<false>(c, a, t, k0, k1, s);
   return cudaGetLastError();
 }
 
 cudaError_t configure_oz_y() {
-  return cudaFuncSetAttribute(ozy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSmem);
+  cudaError_t e = cudaFuncSetAttribute(ozy_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ozy_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSmem);
+  return e;
 }
 
 }  // namespace fermi

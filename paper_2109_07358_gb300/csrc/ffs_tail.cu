@@ -338,16 +338,26 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
     const A uj = (jl < k) ? urow[mrow[jl]] : T::zero();
     const int jn = (int)min((int64_t)32, k - j0);
     int jj = 0;
-    // one group of lookahead: the next group's loads are issued before this group's
-    // stores (the compiler cannot move them across the stores on its own)
+    // one group of lookahead for 4- and 8-byte entries: the next group's loads are issued
+    // before this group's stores (the compiler cannot move them across the stores on its
+    // own); 16-byte (complex double-float / FP64) entries load each group in turn, which
+    // keeps them at 64 registers without spilling
+    constexpr bool kAhead = sizeof(A) <= 8;
     A wv[G];
+    if constexpr (kAhead) {
 #pragma unroll
-    for (int q = 0; q < G; ++q) wv[q] = (need && G <= jn) ? Wp[(j0 + q) * 32 + lane] : T::zero();
+      for (int q = 0; q < G; ++q) wv[q] = (need && G <= jn) ? Wp[(j0 + q) * 32 + lane] : T::zero();
+    }
     for (; jj + G <= jn; jj += G) {
       A wnx[G];
       const bool more = jj + 2 * G <= jn;
+      if constexpr (kAhead) {
 #pragma unroll
-      for (int q = 0; q < G; ++q) wnx[q] = (need && more) ? Wp[(j0 + jj + G + q) * 32 + lane] : T::zero();
+        for (int q = 0; q < G; ++q) wnx[q] = (need && more) ? Wp[(j0 + jj + G + q) * 32 + lane] : T::zero();
+      } else {
+#pragma unroll
+        for (int q = 0; q < G; ++q) wv[q] = need ? Wp[(j0 + jj + q) * 32 + lane] : T::zero();
+      }
       if (keep && live) {
 #pragma unroll
         for (int q = 0; q < G; ++q) W0P[(j0 + jj + q) * NB + lane] = wv[q];
@@ -367,8 +377,10 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
         acc = T::fms(acc, shfl_idx_any(uj, jj + q), gem ? wv[q] : T::zero());
         acc2 = T::fms(acc2, shfl_idx_any(uj, jj + q + 1), gem ? wv[q + 1] : T::zero());
       }
+      if constexpr (kAhead) {
 #pragma unroll
-      for (int q = 0; q < G; ++q) wv[q] = wnx[q];
+        for (int q = 0; q < G; ++q) wv[q] = wnx[q];
+      }
     }
     for (; jj < jn; ++jj) {
       const int64_t j = j0 + jj;

@@ -1,10 +1,13 @@
-"""The tensor-core trailing update (FFS_TRAILING_TC): the old rows' once-per-panel update
-through BF16 slices on tcgen05 must give the double-float state of the direct update to
-within double-float rounding.  The conditionals (FP32 outputs of a BF16x3 residual, whose
-operand split can move by one BF16 unit when the state moves by a rounding) then agree
-with the direct path to 1e-7 and with the oracle within the chosen form's 1e-4; cases cover one and several 128-row
-tiles of old rows, ragged trailing slabs, L-ensemble chains that end inside panels, the
-grouped form, real and complex states, and the full-size lattice."""
+"""The tensor-core trailing update (FFS_TRAILING_TC): the once-per-panel update of the
+blocked state through exact BF16 slices on tcgen05 — the new rows Y = U - C W0_T,
+Bot = S^-1 Y and the old rows Top = W0_T - W0_P Bot, real and complex — must give the
+double-float state of the direct update to within double-float rounding.  The
+conditionals (FP32 outputs of a BF16x3 residual, whose operand split can move by one
+BF16 unit when the state moves by a rounding) then agree with the direct path to 1e-7
+and with the oracle within the chosen form's 1e-4; cases cover one and several 128-row
+tiles of old rows, several 64-row (real) or 32-row (complex) chunks of the new-row
+product (its rings wrap), ragged trailing slabs, L-ensemble chains that end inside
+panels, the grouped form, real and complex states, and the full-size lattice."""
 import numpy as np
 import pytest
 import torch
