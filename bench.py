@@ -52,8 +52,8 @@ WORKLOADS = {
     "anderson_L16384_N2048_B8192": dict(
         make="anderson", B=8192, L=16384, N=2048, cplx=False, grid=(1, 16384),
         desc="1D open Anderson chain L=16384, on-site disorder U[-1, 1] (seed 0), N=2048 lowest orbitals, "
-             "real, B=8192 samples, Philox seed 0 (the precision workload; the per-sample state is 34 MB, "
-             "so the batch runs in waves)"),
+             "real, B=8192 samples, Philox seed 0 (the precision workload; the per-sample double-float "
+             "state is 16.8 MB in triangular slabs, so the whole batch runs in one wave)"),
     "anderson_L4096_N512_B2048": dict(
         make="anderson4k", B=2048, L=4096, N=512, cplx=False, grid=(1, 4096),
         desc="1D open Anderson chain L=4096, on-site disorder U[-1, 1] (seed 0), N=512 lowest orbitals, real, "
@@ -148,12 +148,13 @@ def blocked_flops_per_sample(N, cplx, nb=32):
     return {"step": step * f, "panel_s": panel_s * f, "panel": panel * f, "top": top * f}
 
 
-def blocked_bytes_per_sample(L, N, e, nb=32):
+def blocked_bytes_per_sample(L, N, e, nb=32, gsum=0):
     """Algorithmic HBM bytes per sample of the memory-bound kernels of the blocked state
     update (e = bytes per state entry: 8 for real double-float or FP64, 16 for complex):
-      step  per step k: the L FP32 weights read by the draw; the live panel block read
-            (k x (k1 - k) entries) and written back (k x (k1 - k - 1)); at the first step
-            of a panel the k0 x nb copy W0_P written;
+      step  per step k: what the draw reads (the L FP32 weights, or with gsum > 0 the
+            residual's sums over groups of gsum sites and the chosen group's weights);
+            the live panel block read (k x (k1 - k) entries) and written back
+            (k x (k1 - k - 1)); at the first step of a panel the k0 x nb copy W0_P written;
       new   per panel, T = [k1, N): W0_T read (k0 x |T|), the new rows' U entries read and
             the new rows written (2 x nb x |T|);
       top   per panel: W0_T read and Top written (2 x k0 x |T|), W0_P read (k0 x nb)."""
@@ -161,7 +162,7 @@ def blocked_bytes_per_sample(L, N, e, nb=32):
     for k in range(N):
         k0 = (k // nb) * nb
         k1 = min(k0 + nb, N)
-        step += 4.0 * L
+        step += 4.0 * ((L + gsum - 1) // gsum + gsum) if gsum else 4.0 * L
         if k + 1 < N:
             step += e * (k * (k1 - k) + k * (k1 - k - 1) + (k0 * nb if k == k0 else 0))
     for k0 in range(0, N, nb):
@@ -657,7 +658,8 @@ def phase_report(prof, L, N, B, K, cplx, chosen, state, peaks, trailing_tc):
             "algorithmic": "the paper's 2Lk flops per sample-step, L N (N+1) per sample" + (" x4 complex" if cplx else ""),
             "per_launch": "algorithmic flops of all residual launches / their summed CUDA-event time"}
     e = {"df64": 8, "fp64": 8, "fp32": 4}[state] * (2 if cplx else 1)
-    bb = {k: v * B * K for k, v in blocked_bytes_per_sample(L, N, e).items()}
+    gsum = 0 if chosen == "fp32" else (16 if cplx else 32)  # the tensor-core residual writes group sums
+    bb = {k: v * B * K for k, v in blocked_bytes_per_sample(L, N, e, gsum=gsum).items()}
 
     def gbs(by, ms):
         return by / (ms / 1e3) / 1e9 if ms else None
@@ -698,7 +700,13 @@ def phase_report(prof, L, N, B, K, cplx, chosen, state, peaks, trailing_tc):
                      "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": a_gbs / peaks["hbm_gbs"] if a_gbs else None, "traffic": None,
                      "peak_source": f"{peaks['source']} hbm_gbs (copy bandwidth)",
-                     "algorithmic": blocked_bytes_per_sample.__doc__.split("\n")[0].strip() + f" (e = {e} bytes)",
+                     "algorithmic": {"tail_step": "per sample-step: the weights' group sums and the chosen group (or "
+                                                  "all L weights), the live panel block read and written back, W0_P "
+                                                  "at a panel's first step",
+                                     "tail_panel": "per sample-panel: W0_T read, the new rows' U entries read and the new "
+                                                   "rows written",
+                                     "tail_panel_tc": "per sample-panel: W0_T read and Top written, W0_P read"}[dom]
+                                    + f" ({e}-byte entries)",
                      "share_of_step": cands[dom] / total_ms}
         launches = int(res_n + tail_n + panel_n + pans_n + ptc_n + perm_n) // K
         return phases, roof, roof_tail, launches

@@ -98,6 +98,7 @@ static size_t per_sample_bytes_nc(const ffs_ctx* c, int64_t Nc) {
   b += (size_t)c->ldMask * 4;                      // mask
   b += (size_t)c->Kp * op_elem_bytes(op);          // operand planes
   b += (size_t)c->ldP * 4;                         // weights
+  b += (size_t)c->ldG * 4;                         // their group sums
   b += state_entries(c, Nc) * state_elem_bytes(c);  // elimination state
   b += 8;                                          // logp
   if (blocked(c)) {                                // panel-start columns, panel inverse
@@ -113,6 +114,7 @@ static void free_workspace(ffs_ctx* c) {
   cudaFree(c->mask);
   cudaFree(c->H);
   cudaFree(c->P);
+  cudaFree(c->G);
   cudaFree(c->W);
   cudaFree(c->W0P);
   cudaFree(c->Sinv);
@@ -123,6 +125,7 @@ static void free_workspace(ffs_ctx* c) {
   c->mask = nullptr;
   c->H = nullptr;
   c->P = nullptr;
+  c->G = nullptr;
   c->W = nullptr;
   c->logp = nullptr;
   c->ws_B = 0;
@@ -147,6 +150,7 @@ static int ensure_workspace_nc(ffs_ctx* c, int64_t Bw, int64_t Nc) {
   FFS_CUDA_TRY(c, cudaMalloc((void**)&c->mask, (size_t)B * c->ldMask * 4));
   if (op != kOpNone) FFS_CUDA_TRY(c, cudaMalloc(&c->H, (size_t)B * c->Kp * op_elem_bytes(op)));
   FFS_CUDA_TRY(c, cudaMalloc((void**)&c->P, (size_t)B * c->ldP * 4));
+  FFS_CUDA_TRY(c, cudaMalloc((void**)&c->G, (size_t)B * c->ldG * 4));
   FFS_CUDA_TRY(c, cudaMalloc(&c->W, wb));
   FFS_CUDA_TRY(c, cudaMalloc((void**)&c->logp, (size_t)B * 8));
   if (blocked(c)) {
@@ -319,6 +323,7 @@ int ffs_create_ex(const void* U, int dtype, int64_t L, int64_t N, int64_t ldU, u
   c->Kp = round_up(c->Kr, 64);
   c->Lrp = round_up(c->Lr, 256);
   c->ldP = round_up(L, 4);
+  c->ldG = round_up((L + 15) / 16, 4);  // group sums of at most 16 sites each
   c->ldMask = (L + 31) / 32;
 
   // FP64 copy of U
@@ -493,6 +498,10 @@ static int sample_core(ffs_ctx* h, int64_t B, uint64_t seed, uint64_t first_samp
     a.H = h->H;
     a.hplane = h->ws_B * h->Kp;
     a.P = h->P;
+    if (!plain && op != kOpF32) {  // the tensor-core residual writes the weights' group sums
+      a.G = h->G;
+      a.ldG = h->ldG;
+    }
     a.W = h->W;
     a.logp = h->logp;
     a.x = x_dev ? out_x + b0 * ldx : xbuf;

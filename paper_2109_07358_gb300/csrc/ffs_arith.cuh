@@ -85,9 +85,45 @@ __device__ __forceinline__ void lz_mac(lzf& a, df x, df y) {  // a += x y
   a.hi = s;
   a.lo = __fadd_rn(a.lo, __fadd_rn(err, __fadd_rn(e, cr)));
 }
+// a += x for an FP32 x: the error-free sum of the high parts, its error added to lo
+// (seven instructions, no renormalising).
+__device__ __forceinline__ void lz_add(lzf& a, float x) {
+  const float s = __fadd_rn(a.hi, x);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, err);
+}
 __device__ __forceinline__ df lz_get(lzf a) {
   const df s = two_sum(a.hi, a.lo);
   return quick_two_sum(s.hi, s.lo);
+}
+
+// The value V = sum_{d=2..8} G_d 2^(-8(d-2)) of the seven group accumulators of an Ozaki
+// slice product (G_d = sum of the slice products a_i b_j with i + j = d: integers of at
+// most 2^23, exact in FP32), for NV outputs at once; ld(d, r) reads G_d into r.  Smallest
+// groups first: G_8, G_7 and G_6 in FP32 (one rounding of at most half a unit of G_6,
+// 2^-33 of a unit of G_2), then G_5 .. G_2 by lazy error-free sums (seven instructions
+// each instead of the twelve of a renormalised double-float addition).
+template <int NV, typename Ld>
+__device__ __forceinline__ void oz_group_sum(Ld ld, lzf (&S)[NV]) {
+  uint32_t r[NV];
+  ld(8, r);
+#pragma unroll
+  for (int n = 0; n < NV; ++n) S[n].hi = __uint_as_float(r[n]) * 0x1p-16f;
+  ld(7, r);
+#pragma unroll
+  for (int n = 0; n < NV; ++n) S[n].hi = __fmaf_rn(__uint_as_float(r[n]), 0x1p-8f, S[n].hi);
+  ld(6, r);
+#pragma unroll
+  for (int n = 0; n < NV; ++n) S[n] = lzf{__fadd_rn(__uint_as_float(r[n]), S[n].hi) * 0x1p-32f, 0.f};
+#pragma unroll 1
+  for (int d = 5; d >= 2; --d) {
+    ld(d, r);
+    const float p2 = ldexpf(1.f, -8 * (d - 2));
+#pragma unroll
+    for (int n = 0; n < NV; ++n) lz_add(S[n], __uint_as_float(r[n]) * p2);
+  }
 }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 

@@ -190,6 +190,7 @@ struct ffs_ctx {
   uint32_t* mask = nullptr;      // Bw x ceil(L/32) chosen-site bits
   void* H = nullptr;             // Bw x Kp residual operand (per-mode element type / planes)
   float* P = nullptr;            // Bw x ldP masked weights |u_y^T h|^2 of the current step
+  float* G = nullptr;            // Bw x ldG their sums per group of 32 (real) or 16 (complex) sites
   void* W = nullptr;             // elimination state (state precision): Bw x N x N unblocked,
                                  // Bw x Nc x round_up(Nc, 32) in 32-column slabs when blocked
   void* W0P = nullptr;           // Bw x N x 32 old rows' panel columns at the panel start
@@ -202,6 +203,7 @@ struct ffs_ctx {
   float* probsbuf = nullptr;     // Bw x n_steps x L (only when asked)
   int64_t probs_cap = 0;
   int64_t ldP = 0;
+  int64_t ldG = 0;
   int64_t ldMask = 0;
 
   // TMA descriptors of the tensor-core residual: the two planes of Ue and of H.

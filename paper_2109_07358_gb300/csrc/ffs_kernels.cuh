@@ -28,6 +28,11 @@ struct StepArgs {
   void* H;                 // bw x Kp operand planes
   int64_t hplane;          // elements per operand plane (capacity x Kp)
   float* P;                // bw x ldP
+  // bw x ldG sums of the weights per group of kGroupSites(cplx) sites, written by the
+  // tensor-core residual next to P (null when the residual form does not write them);
+  // the draw then reads the sums instead of all L weights
+  float* G = nullptr;
+  int64_t ldG = 0;
   void* W;                 // bw x N x N state
   double* logp;            // bw
   int32_t* x;              // bw x ldx
@@ -41,6 +46,10 @@ struct StepArgs {
   int grouped;             // groups of 128 samples share m; h is stored in the group's order
   int64_t kcols;           // residual K columns in use (grouped form), 0 = all
 };
+
+// Sites per weight-group sum: the 32 accumulator columns of one residual epilogue load,
+// 32 real sites or 16 complex ones (a site's real and imaginary parts are adjacent columns).
+__host__ __device__ __forceinline__ int kGroupSites(bool cplx) { return cplx ? 16 : 32; }
 
 // Operand column of entry j of h: the original column m_j, or position j when the group's
 // copy of the embedding is already in its column order.

@@ -325,22 +325,18 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_kernel(const __grid_consta
       const int64_t c0 = k1 + (int64_t)nt * NT;
       if (ok) tc_fence_after();
       for (int part = 0; part < (CX ? 2 : 1) && ok; ++part) {  // real, then imaginary part of the product
-        df S[kEpiCols];
-#pragma unroll
-        for (int n = 0; n < kEpiCols; ++n) S[n] = df{0.f, 0.f};
-        for (int d = kDmax; d >= 2; --d) {  // smallest terms first
-          uint32_t r[kEpiCols];
-          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * (part * kNumD + d - 2) + kEpiCols * h), r);
-          tmem_ld_wait();
-          const float p2 = ldexpf(1.f, -8 * (d - 2));
-#pragma unroll
-          for (int n = 0; n < kEpiCols; ++n) S[n] = df_add(S[n], df{__uint_as_float(r[n]) * p2, 0.f});
-        }
+        lzf S[kEpiCols];
+        oz_group_sum<kEpiCols>(
+            [&](int d, uint32_t(&r)[kEpiCols]) {
+              tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * (part * kNumD + d - 2) + kEpiCols * h), r);
+              tmem_ld_wait();
+            },
+            S);
 #pragma unroll
         for (int n = 0; n < kEpiCols; ++n) {
           const int64_t c = c0 + kEpiCols * h + n;
           const float scale = (c < Nc) ? sr * z.Bs[(size_t)b * z.TP + c] * 0x1p-14f : 0.f;
-          *(df*)(Pq + lane * kPRow + (kEpiCols * h + n) * 16 + part * 8) = df_scale(S[n], scale);
+          *(df*)(Pq + lane * kPRow + (kEpiCols * h + n) * 16 + part * 8) = df_scale(lz_get(S[n]), scale);
         }
       }
       tc_fence_before();
@@ -577,25 +573,32 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_real_kernel(const __grid_c
     bool dead = false;
     for (int nt = 0; nt < n_tiles; ++nt) {
       const int u = nt & 1;
+      const int64_t c0 = k1 + (int64_t)nt * NT;
+      // this warp's rows of the slab (lanes over columns) are loaded before the wait for the
+      // accumulators: they do not depend on the products, so their latency overlaps the MMAs
+      // and the group sums
+      df* Wc = (df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c0 >> 5);
+      df wv[kEpiCols];
+#pragma unroll
+      for (int n = 0; n < kEpiCols; ++n) {
+        const int64_t jr = mt * MT + 32 * q + kEpiCols * h + n;
+        wv[n] = (jr < k0 && c0 + lane < Nc) ? Wc[jr * 32 + lane] : df{0.f, 0.f};
+      }
       const bool ok = !dead && mbar_wait(acc_full(u), (nt >> 1) & 1, abort_flag);
       if (!ok && !dead) {
         fail();
         dead = true;
       }
-      const int64_t c0 = k1 + (int64_t)nt * NT;
       if (ok) {
         tc_fence_after();
-        df S[kEpiCols];
-#pragma unroll
-        for (int n = 0; n < kEpiCols; ++n) S[n] = df{0.f, 0.f};
-        for (int d = kDmax; d >= 2; --d) {  // smallest terms first
-          uint32_t r[kEpiCols];
-          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)u * kRAccCols + (uint32_t)(32 * (d - 2) + kEpiCols * h), r);
-          tmem_ld_wait();
-          const float p2 = ldexpf(1.f, -8 * (d - 2));
-#pragma unroll
-          for (int n = 0; n < kEpiCols; ++n) S[n] = df_add(S[n], df{__uint_as_float(r[n]) * p2, 0.f});
-        }
+        lzf S[kEpiCols];
+        oz_group_sum<kEpiCols>(
+            [&](int d, uint32_t(&r)[kEpiCols]) {
+              tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)u * kRAccCols + (uint32_t)(32 * (d - 2) + kEpiCols * h),
+                       r);
+              tmem_ld_wait();
+            },
+            S);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty(u));  // the accumulators may be overwritten now
@@ -603,19 +606,11 @@ __global__ void __launch_bounds__(kThreads, 1) oz_top_real_kernel(const __grid_c
         for (int n = 0; n < kEpiCols; ++n) {
           const int64_t c = c0 + kEpiCols * h + n;
           const float scale = (c < Nc) ? sr * z.Bs[(size_t)b * z.TP + c] * 0x1p-14f : 0.f;
-          *(df*)(Pq + lane * kRPRow + (kEpiCols * h + n) * 8) = df_scale(S[n], scale);
+          *(df*)(Pq + lane * kRPRow + (kEpiCols * h + n) * 8) = df_scale(lz_get(S[n]), scale);
         }
       }
       named_sync(quarter_bar, quarter_threads);  // all the quarter's columns are staged
-      df* Wc = (df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c0 >> 5);
       const bool col_ok = ok && c0 + lane < Nc;
-      // all the warp's rows are loaded before any is stored, so that their loads overlap
-      df wv[kEpiCols];
-#pragma unroll
-      for (int n = 0; n < kEpiCols; ++n) {
-        const int64_t jr = mt * MT + 32 * q + kEpiCols * h + n;
-        wv[n] = (jr < k0 && col_ok) ? Wc[jr * 32 + lane] : df{0.f, 0.f};
-      }
 #pragma unroll
       for (int n = 0; n < kEpiCols; ++n) {
         const int rr = kEpiCols * h + n;

@@ -5,21 +5,25 @@
 //   Y   = U[x_new, m_T] - C W0_T,   C = U[x_new, m_<k0]   (32 x |T|, K = k0)
 //   Bot = S^-1 Y                                          (written as state rows k0..k1-1)
 // Y holds most of the panel end's multiply-adds (32 k0 |T| per sample).  Here it runs on
-// tcgen05 as Y^T = D^T - W0_T^T C^T through an error-free split of both double-float
-// operands into BF16 slices (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012):
+// tcgen05 as Y^T = D^T - W0_T^T C^T through a split of both double-float operands into
+// BF16 slices (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012):
 //   * K (the old rows j < k0) is cut into chunks of 64.  Within a chunk, trailing column c
 //     of W0_T is scaled by a power of two sigma_{c,t} >= its largest entry and cut into six
-//     8-bit integer slices, W0_T[j, c] / sigma = sum_i a_i 2^(-7 - 8(i-1)), |a_i| <= 128
-//     (exact in BF16); row i of C likewise with sigma_{i,t};
+//     8-bit integer slices, W0_T[j, c] / sigma = sum_i a_i 2^(-7 - 8(i-1)) + r, |r| <=
+//     2^-47 (three exact digits of the high part, then the low part folded into the
+//     remainder by one FMA; |a_i| <= 128 except |a_4| <= 256, all exact in BF16); row i
+//     of C likewise with sigma_{i,t}, by error-free steps (|r| <= 2^-48);
 //   * the 26 slice products a_i b_j with i + j = d <= 8 accumulate in one FP32 accumulator
-//     per d in tensor memory: 64 products of at most 2^14 each, integers below 2^21, so
-//     the tensor-core accumulation is exact;
-//   * per chunk the epilogue adds the seven accumulators in double-float, scales by
-//     sigma_{c,t} sigma_{i,t} 2^-14 2^(-8(d-2)) and accumulates the chunk into Y;
+//     per d in tensor memory: 64 products of at most 2^15 each, integers of at most 2^23,
+//     so the tensor-core accumulation is exact;
+//   * per chunk the epilogue adds the seven accumulators (oz_group_sum), scales by
+//     sigma_{c,t} sigma_{i,t} 2^-14 and accumulates the chunk into Y;
 //   * the accumulators are double-buffered, so one chunk's epilogue overlaps the next
 //     chunk's products.
-// The dropped products (i + j > 8) are below 2^-56 of sigma sigma per term, beneath the
-// double-float rounding of the direct update.
+// The remainders (3/4 of 2^-46 sigma sigma per term), the dropped products (i + j > 8,
+// below 2^-53 sigma sigma per term) and the FP32 rounding of the three smallest groups
+// (2^-47 sigma sigma per chunk) keep each chunk's product within 2^-46 sigma sigma K of
+// the exact one, next to the double-float rounding of the direct update.
 //
 // CTA: one sample, 128 trailing columns.  Warp 0 issues the TMA loads of C's slices (made
 // once per sample and panel by ozc_slice_kernel), warp 1 allocates tensor memory and
@@ -340,22 +344,33 @@ __global__ void __launch_bounds__(kYThreads, 1)
       if constexpr (CX) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));  // both rows of the column
       float sigma, inv;
       ypow2(mx, sigma, inv);
-      // x / sigma first, then 2^7: inv alone can be 2^125, so inv 2^7 would overflow
+      // The six slices with three instructions each (against seven for slice_step): the
+      // first three digits come from th = hi / sigma 2^7 alone (each remainder th - a is
+      // exact and, scaled by 2^8, again at most 2^7); then the low part joins the remainder
+      // in one FMA, th + (lo / sigma) 2^31, whose rounding (half an ulp, at most 2^-48 sigma)
+      // and the remainder dropped after the sixth digit (at most 2^-48 sigma) are the only
+      // errors.  That sum is at most 256, so the fourth digit is too: still exact in BF16.
+      // x / sigma first, then 2^7: inv alone can be 2^125, so inv 2^7 would overflow.
 #pragma unroll
       for (int e = 0; e < 32; ++e) {
         th[e] = __fmul_rn(__fmul_rn(th[e], inv), 128.f);
-        tl[e] = __fmul_rn(__fmul_rn(tl[e], inv), 128.f);
+        tl[e] = __fmul_rn(tl[e], inv);
       }
       const int rs = tc & (kYSigRing - 1);
       if (q == 0) sSig[rs * YM + ar] = sigma;
       __syncwarp();
       if (lane == 0) mbar_arrive(sig_full(rs));
       bool ok = true;
+#pragma unroll 1
       for (int hf = 0; hf < 2; ++hf) {
         const int hidx = 2 * tc + hf, slot = hidx % kYAHalves;
         if (hidx >= kYAHalves && !mbar_wait(a_empty(slot), ((hidx / kYAHalves) - 1) & 1, abort_flag)) {
           ok = false;
           break;
+        }
+        if (hf == 1) {  // digits 4..6: the remainder of hi with the low part
+#pragma unroll
+          for (int e = 0; e < 32; ++e) th[e] = __fmaf_rn(tl[e], 0x1p31f, th[e]);
         }
         const uint32_t stA = sA + slot * kYAHalf;
 #pragma unroll
@@ -365,9 +380,14 @@ __global__ void __launch_bounds__(kYThreads, 1)
             uint32_t w4[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              const float x0 = slice_step(th[8 * g + 2 * e], tl[8 * g + 2 * e]);
-              const float x1 = slice_step(th[8 * g + 2 * e + 1], tl[8 * g + 2 * e + 1]);
-              w4[e] = pack_bf16x2(x0, x1);
+              float x[2];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                float& v = th[8 * g + 2 * e + h];
+                x[h] = rintf(v);
+                if (3 * hf + s < kYS - 1) v = __fmul_rn(__fsub_rn(v, x[h]), 256.f);
+              }
+              w4[e] = pack_bf16x2(x[0], x[1]);
             }
             const uint32_t addr = stA + s * kYATile + sw128_chunk((uint32_t)ar, (uint32_t)(4 * q + g));
             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w4[0]), "r"(w4[1]), "r"(w4[2]),
@@ -395,9 +415,9 @@ __global__ void __launch_bounds__(kYThreads, 1)
     const int rpart = CX ? (ar & 1) : 0;       // complex: 0 = Re, 1 = Im of the product
     const int64_t c = c0 + cl;
     const bool cval = c < Nc;
-    df yacc[16];
+    lzf yacc[16];
 #pragma unroll
-    for (int n = 0; n < 16; ++n) yacc[n] = df{0.f, 0.f};
+    for (int n = 0; n < 16; ++n) yacc[n] = lzf{0.f, 0.f};
     bool dead = false;
     for (int tc = 0; tc < nch; ++tc) {
       const int u = tc & 1;
@@ -410,18 +430,14 @@ __global__ void __launch_bounds__(kYThreads, 1)
         break;
       }
       tc_fence_after();
-      df S[16];
-#pragma unroll
-      for (int n = 0; n < 16; ++n) S[n] = df{0.f, 0.f};
-#pragma unroll 1
-      for (int d = kYD; d >= 2; --d) {  // smallest terms first
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)u * kYAccCols + (uint32_t)(32 * (d - 2) + 16 * hh), r);
-        tmem_ld_wait();
-        const float p2 = ldexpf(1.f, -8 * (d - 2));
-#pragma unroll
-        for (int n = 0; n < 16; ++n) S[n] = df_add(S[n], df{__uint_as_float(r[n]) * p2, 0.f});
-      }
+      lzf S[16];
+      oz_group_sum<16>(
+          [&](int d, uint32_t(&r)[16]) {
+            tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)u * kYAccCols + (uint32_t)(32 * (d - 2) + 16 * hh),
+                      r);
+            tmem_ld_wait();
+          },
+          S);
       // the chunk's column scale is read before the accumulators are released: a producer
       // can overwrite its ring slot only after that release (four chunks later)
       const float sc = sSig[rs * YM + ar] * 0x1p-14f;
@@ -432,7 +448,8 @@ __global__ void __launch_bounds__(kYThreads, 1)
 #pragma unroll
       for (int n = 0; n < 16; ++n) {
         const float f = sc * cs[n];  // a power of two
-        yacc[n] = df_add(yacc[n], df{S[n].hi * f, S[n].lo * f});
+        lz_add(yacc[n], S[n].hi * f);
+        yacc[n].lo = __fmaf_rn(S[n].lo, f, yacc[n].lo);
       }
     }
     // Y = U[x_new, m_c] - (C W0_T)[:, c], staged for Bot = S^-1 Y
@@ -449,7 +466,7 @@ __global__ void __launch_bounds__(kYThreads, 1)
         if (cval) {
           const int xi = a.x[b * a.ldx + k0 + i];
           const cdf d = ((const cdf*)a.Ust)[(int64_t)xi * a.N + mc];
-          y = df_sub(rpart ? d.im : d.re, yacc[n]);
+          y = df_sub(rpart ? d.im : d.re, lz_get(yacc[n]));
         }
         ((df*)&Ys[i * YCOL + cl])[rpart] = y;
       }
@@ -458,19 +475,27 @@ __global__ void __launch_bounds__(kYThreads, 1)
       if (cval) {
         // this thread's 8 of the column's 32 new rows: Bot = S^-1 Y in four real products
         cdf* Wn = (cdf*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
+        // two rows at a time (four independent accumulation chains)
 #pragma unroll 1
-        for (int n = 0; n < 8; ++n) {
-          const int i = 16 * hh + 8 * rpart + n;
-          lzf re{0.f, 0.f}, im{0.f, 0.f};
-#pragma unroll 4
+        for (int n0 = 0; n0 < 8; n0 += 2) {
+          const int i0 = 16 * hh + 8 * rpart + n0;
+          lzf re[2], im[2];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) re[r] = im[r] = lzf{0.f, 0.f};
+#pragma unroll 1
           for (int ip = 0; ip < YN; ++ip) {
-            const cdf sv = Si[i * YN + ip], yv = Ys[ip * YCOL + cl];
-            lz_mac(re, sv.re, yv.re);
-            lz_mac(re, df_neg(sv.im), yv.im);
-            lz_mac(im, sv.re, yv.im);
-            lz_mac(im, sv.im, yv.re);
+            const cdf yv = Ys[ip * YCOL + cl];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              const cdf sv = Si[(i0 + r) * YN + ip];
+              lz_mac(re[r], sv.re, yv.re);
+              lz_mac(re[r], df_neg(sv.im), yv.im);
+              lz_mac(im[r], sv.re, yv.im);
+              lz_mac(im[r], sv.im, yv.re);
+            }
           }
-          Wn[(k0 + i) * 32] = cdf{lz_get(re), lz_get(im)};
+#pragma unroll
+          for (int r = 0; r < 2; ++r) Wn[(k0 + i0 + r) * 32] = cdf{lz_get(re[r]), lz_get(im[r])};
         }
       }
     } else {
@@ -482,7 +507,7 @@ __global__ void __launch_bounds__(kYThreads, 1)
         df y = df{0.f, 0.f};
         if (cval) {
           const int xi = a.x[b * a.ldx + k0 + i];
-          y = df_sub(((const df*)a.Ust)[(int64_t)xi * a.N + mc], yacc[n]);
+          y = df_sub(((const df*)a.Ust)[(int64_t)xi * a.N + mc], lz_get(yacc[n]));
         }
         Ys[i * YM + cl] = y;
       }
@@ -490,13 +515,21 @@ __global__ void __launch_bounds__(kYThreads, 1)
       named_sync(1, 32 * kYEpiWarps);
       if (cval) {
         df* Wn = (df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
+        // four rows at a time: four independent accumulation chains share each Y entry
 #pragma unroll 1
-        for (int n = 0; n < 16; ++n) {
-          const int i = 16 * hh + n;
-          lzf acc{0.f, 0.f};
-#pragma unroll 8
-          for (int ip = 0; ip < YN; ++ip) lz_mac(acc, Si[i * YN + ip], Ys[ip * YM + cl]);
-          Wn[(k0 + i) * 32] = lz_get(acc);
+        for (int n0 = 0; n0 < 16; n0 += 4) {
+          const int i0 = 16 * hh + n0;
+          lzf acc[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[r] = lzf{0.f, 0.f};
+#pragma unroll 2
+          for (int ip = 0; ip < YN; ++ip) {
+            const df yv = Ys[ip * YM + cl];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) lz_mac(acc[r], Si[(i0 + r) * YN + ip], yv);
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r) Wn[(k0 + i0 + r) * 32] = lz_get(acc[r]);
         }
       }
     }

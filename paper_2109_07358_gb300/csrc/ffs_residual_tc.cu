@@ -49,6 +49,21 @@ struct TcCfg {
   static constexpr uint32_t IDESC = (KIND == kKindTF32) ? idesc_tf32(BM, BN) : idesc_bf16(BM, BN);
 };
 
+// Sum of the n weights of one site group by a balanced tree (the draw adds these group
+// sums in site order for the normaliser and the search).
+template <int n>
+__device__ __forceinline__ float group_sum_w(const float (&w)[n]) {
+  float t[n / 2];
+#pragma unroll
+  for (int i = 0; i < n / 2; ++i) t[i] = w[2 * i] + w[2 * i + 1];
+#pragma unroll
+  for (int m = n / 4; m >= 1; m /= 2) {
+#pragma unroll
+    for (int i = 0; i < m; ++i) t[i] = t[2 * i] + t[2 * i + 1];
+  }
+  return t[0];
+}
+
 // One output tile (samples [b0, b0+128) x embedding columns [j0, j0+BN)) of one
 // instance; the tensor maps may live in kernel parameters or in global memory.
 template <int BN, int STAGES, int KIND>
@@ -199,8 +214,11 @@ __device__ __forceinline__ void residual_body(const CUtensorMap* tmA0p, const CU
           for (int i = 0; i < 16; i += 4)
             *(float4*)(prow + y0 + i) = make_float4(w[i], w[i + 1], w[i + 2], w[i + 3]);
         } else {
-          for (int i = 0; i < 16 && y0 + i < p.L; ++i) prow[y0 + i] = w[i];
+          for (int i = 0; i < 16; ++i)
+            if (y0 + i < p.L) prow[y0 + i] = w[i];
+            else w[i] = 0.f;
         }
+        if (p.G) p.G[b * p.ldG + (y0 >> 4)] = group_sum_w<16>(w);
       } else {
         const int64_t y0 = (int64_t)j0 + 32 * c;  // 32 sites
         if (y0 >= p.L) continue;
@@ -216,8 +234,11 @@ __device__ __forceinline__ void residual_body(const CUtensorMap* tmA0p, const CU
           for (int i = 0; i < 32; i += 4)
             *(float4*)(prow + y0 + i) = make_float4(w[i], w[i + 1], w[i + 2], w[i + 3]);
         } else {
-          for (int i = 0; i < 32 && y0 + i < p.L; ++i) prow[y0 + i] = w[i];
+          for (int i = 0; i < 32; ++i)
+            if (y0 + i < p.L) prow[y0 + i] = w[i];
+            else w[i] = 0.f;
         }
+        if (p.G) p.G[b * p.ldG + (y0 >> 5)] = group_sum_w<32>(w);
       }
     }
   }
@@ -361,6 +382,8 @@ static cudaError_t launch_cfg(ffs_ctx* c, const StepArgs& a, cudaStream_t s) {
   p.cplx = a.cplx ? 1 : 0;
   p.grp_rows = a.grouped ? (int)c->Lrp : 0;
   p.P = a.P;
+  p.G = a.G;
+  p.ldG = a.ldG;
   p.mask = a.mask;
   p.status = a.status;
   if (c->debug_fault == FFS_FAULT_SKIP_ARRIVAL) {  // one-shot, armed by ffs_debug_inject

@@ -12,6 +12,8 @@ struct TcArgs {
   int cplx;
   int grp_rows;  // grouped form: rows of one group's copy of Ue (row offset of sample tile t: t x grp_rows)
   float* P;
+  float* G = nullptr;  // or the sums of the weights per 32 accumulator columns (32 real, 16 complex sites)
+  int64_t ldG = 0;
   const uint32_t* mask;
   int* status;
   uint32_t spin = 1u << 18;  // polls before a wait gives up (FFS_E_TIMEOUT); each may suspend 100 us

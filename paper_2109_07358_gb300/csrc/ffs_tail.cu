@@ -188,6 +188,58 @@ __device__ __forceinline__ double chunk_reduce(float4 v) {
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return (double)s;
 }
+// Normaliser from the residual's group sums g[0 .. ng): lane l adds groups l, l + 32, ...
+// in FP64, then a butterfly over the warp (the same value in every lane).
+__device__ __forceinline__ double gsum_total(const float* __restrict__ g, int64_t ng, int lane) {
+  double z = 0.0;
+  int64_t i = lane;
+  for (; i + 96 < ng; i += 128) {  // four loads in flight
+    const float a0 = g[i], a1 = g[i + 32], a2 = g[i + 64], a3 = g[i + 96];
+    z += ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
+  }
+  for (; i < ng; i += 32) z += (double)g[i];
+  for (int o = 16; o; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+  return z;
+}
+
+// Inverse-CDF search over the group sums: blocks of 32 groups (a warp scan in FP64), the
+// first group with a positive sum whose running sum passes t, then the first site of that
+// group (gs sites, one per lane) with a positive weight whose running sum passes t.  When
+// rounding leaves no site of the chosen group past t, its last site with a positive
+// weight; -1 when no group passes t.
+__device__ __forceinline__ int gsum_find(const float* __restrict__ g, const float* __restrict__ p, int64_t L,
+                                         int gs, int lane, double t) {
+  const int64_t ng = (L + gs - 1) / gs;
+  double base = 0.0;
+  for (int64_t g0 = 0; g0 < ng; g0 += 32) {
+    const int64_t gi = g0 + lane;
+    const double v = gi < ng ? (double)g[gi] : 0.0;
+    double incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const double u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, v > 0.0 && base + incl > t);
+    if (hit) {
+      const int src = __ffs(hit) - 1;
+      const double gb = base + __shfl_sync(0xffffffffu, incl - v, src);
+      const int64_t y = (g0 + src) * gs + lane;
+      const double w = (lane < gs && y < L) ? (double)p[y] : 0.0;
+      double run = w;
+      for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, run, o);
+        if (lane >= o) run += u;
+      }
+      const unsigned in = __ballot_sync(0xffffffffu, w > 0.0 && gb + run > t);
+      const unsigned pos = __ballot_sync(0xffffffffu, w > 0.0);
+      if (in) return (int)((g0 + src) * gs + __ffs(in) - 1);
+      if (pos) return (int)((g0 + src) * gs + 31 - __clz(pos));
+    }
+    base += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  return -1;
+}
+
 // Chunk sums of the normaliser pass kept in shared memory for the search pass: up to
 // kCsMax chunks per warp, i.e. L <= 16384; longer rows take the two-pass form.
 constexpr int kCsMax = 128;
@@ -223,11 +275,16 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
   }
 
   // draw: Z over 128-site chunks, then the first chunk whose running sum passes t (both
-  // sums in chunk order; with the chunk sums cached, the search reads only the chosen chunk)
+  // sums in chunk order; with the chunk sums cached, the search reads only the chosen chunk).
+  // When the residual wrote the weights' group sums, Z and the search read those instead
+  // (L / 32 or L / 16 sums) and then the weights of the chosen group alone.
   const int64_t nch = (L + 127) / 128;
-  const bool cached = nch <= kCsMax;
+  const bool grouped_sums = a.G != nullptr;
+  const bool cached = !grouped_sums && nch <= kCsMax;
   double Z = 0.0;
-  if (cached) {
+  if (grouped_sums) {
+    Z = gsum_total(a.G + b * a.ldG, (L + kGroupSites(a.cplx) - 1) / kGroupSites(a.cplx), lane);
+  } else if (cached) {
     for (int64_t ch0 = 0; ch0 < nch; ch0 += 4) {  // four chunks' loads in flight together
       float4 v[4];
 #pragma unroll
@@ -255,7 +312,9 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const BlockedArgs& 
     const double tt = site_uniform(a.seed, a.first + (uint64_t)b, (int)k) * Z;
     x = -1;
     double base = 0.0;
-    if (cached) {
+    if (grouped_sums) {
+      x = gsum_find(a.G + b * a.ldG, prow, L, kGroupSites(a.cplx), lane, tt);
+    } else if (cached) {
       for (int64_t ch = 0; ch < nch && x < 0; ++ch) {
         const double cs = csm[ch];
         if (base + cs > tt) x = chunk_find(prow, L, ch, lane, base, tt);
@@ -325,10 +384,15 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
   // together; two accumulation chains)
   constexpr int G = kStepRowGroup;
   A acc = T::zero(), acc2 = T::zero();
-  // rows stream from DRAM: keep the next 32-row groups on their way into L2 (one bulk
-  // prefetch per group, two groups ahead of the loads)
+  // rows stream from DRAM: keep the next 32-row groups on their way into L2, two groups
+  // ahead of the loads; lane l prefetches row j + l from the first column read (rounded
+  // down to 16 bytes) to the end of the row, so late in a panel, when few columns are
+  // live, the prefetch does not drag the dead part of each row out of DRAM
+  constexpr int kColAlign = sizeof(A) >= 16 ? 1 : (int)(16 / sizeof(A));
+  const int cpf = (i >= 1 ? i - 1 : 0) & ~(kColAlign - 1);
+  const uint32_t pf_bytes = (uint32_t)((32 - cpf) * sizeof(A));
   auto prefetch_rows = [&](int64_t j) {
-    if (lane == 0 && j < k) sm100::prefetch_l2_bulk(Wp + j * 32, (uint32_t)(min((int64_t)32, k - j) * 32 * sizeof(A)));
+    if (j + lane < k) sm100::prefetch_l2_bulk(Wp + (j + lane) * 32 + cpf, pf_bytes);
   };
   prefetch_rows(0);
   prefetch_rows(32);

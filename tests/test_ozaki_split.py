@@ -14,6 +14,12 @@ i + j <= 8 are accumulated per d = i + j in FP32 over K = 64.  The claims:
   2^-46 sigma_r sigma_c K of the exact product;
 * a subnormal maximum takes sigma = 2^-125 and its slices stay finite and exact.
 
+The new rows' kernel slices W0_T more cheaply (three exact digits of the high part, then
+the low part folded into the remainder by one FMA) and adds the seven groups with FP32
+for the three smallest and lazy error-free sums for the rest; for those the claims are a
+remainder of at most 2^-47, a fourth digit of at most 256 (still exact in BF16), group
+sums of at most 2^23, and the chunk's product still within 2^-46 sigma sigma K.
+
 The slicing below is an FP32 restatement of the same steps (numpy float32 rounds to
 nearest even like the kernels' _rn operations); the expected values are exact rationals.
 """
@@ -238,3 +244,121 @@ def test_smallest_scale_keeps_the_scaling_finite():
         s, rem = slices_fast(F(h * inv), F(0.0))
         recon = sum(Fraction(int(a)) * Fraction(1, 2 ** (7 + 8 * i)) for i, a in enumerate(s))
         assert recon + rem * Fraction(1, 2 ** (7 + 8 * SLICES)) == Fraction(float(F(h * inv)))
+
+
+def slices_fold(hi, lo):
+    """The new-row kernel's slicing of W0_T (hi, lo already divided by sigma): three digits
+    of th = hi 2^7 by exact steps (rint, subtract, times 2^8), then the low part joins the
+    remainder in one FMA (th + lo 2^31, a single rounding), then three more digits; the
+    remainder after the sixth digit is dropped."""
+    th = F(hi * F(128))
+    out = []
+    for _ in range(3):
+        a = F(np.rint(th))
+        d = F(th - a)
+        assert Fraction(float(d)) == Fraction(float(th)) - Fraction(float(a))   # exact
+        out.append(a)
+        th = F(d * F(256))
+    # FMA: the exact value th + lo 2^31 (exact in float64: both are short dyadic numbers)
+    # rounded once to FP32
+    th = F(float(th) + float(lo) * 2.0 ** 31)
+    for _ in range(3):
+        a = F(np.rint(th))
+        out.append(a)
+        th = F(F(th - a) * F(256))
+    return out
+
+
+def fold_worst_cases(rng, n):
+    """Values whose folded sum reaches its bound: hi just below sigma with few significant
+    bits (so the remainder after three digits is large) and lo at +-ulp(hi)/2."""
+    hi = (rng.uniform(0.5, 1.0, n) * rng.choice([-1.0, 1.0], n)).astype(F)
+    hi[: n // 2] = (np.round(hi[: n // 2] * 2.0 ** 23) / 2.0 ** 23).astype(F)
+    ulp = np.spacing(np.abs(hi)).astype(F)
+    lo = (rng.choice([-0.5, 0.5, 0.499, -0.499], n) * ulp).astype(F)
+    return hi, lo
+
+
+@pytest.mark.parametrize("gen", ["random", "adversarial", "worst"])
+def test_folded_slicing_error_and_digit_bounds(gen):
+    rng = np.random.default_rng(17)
+    if gen == "random":
+        hi, lo = random_df(rng, 512)
+    elif gen == "adversarial":
+        hi, lo = adversarial_df(rng, 512)
+    else:
+        hi, lo = fold_worst_cases(rng, 512)
+    sigma, inv = pow2_scale(float(np.max(np.abs(hi))))
+    big = 0.0
+    for h, l in zip(hi, lo):
+        s = slices_fold(F(h * inv), F(l * inv))
+        for i, a in enumerate(s):
+            assert float(a).is_integer() and abs(a) <= (256 if i == 3 else 128)   # exact in BF16
+        big = max(big, abs(float(s[3])))
+        recon = sum(Fraction(int(a)) * Fraction(1, 2 ** (7 + 8 * i)) for i, a in enumerate(s))
+        assert abs(recon - exact(F(h * inv), F(l * inv))) <= Fraction(1, 2 ** 47)
+    if gen == "worst":
+        assert big > 128          # the fourth digit does exceed 128 on these inputs
+
+
+def test_folded_group_sums_stay_exact():
+    # |a_4| <= 256 on the W0_T side only; the worst group sums over a 64-row chunk
+    aw = [128, 128, 128, 256, 128, 128]
+    bc = [128] * 6
+    worst = max(sum(aw[i - 1] * bc[d - i - 1] for i in range(1, 7) if 1 <= d - i <= 6) * K for d in range(2, DMAX + 1))
+    assert worst <= 2 ** 23           # integers of at most 2^23: exact in FP32 in any order
+
+
+def group_sum(G):
+    """The epilogue's sum of the seven group accumulators G[d] (d = 2..8, integers): G_8,
+    G_7 and G_6 in FP32 (the FMA rounded once), then G_5 .. G_2 by lazy error-free sums,
+    then one renormalisation (oz_group_sum, lz_get)."""
+    t = F(float(F(G[8])) * 2.0 ** -16)
+    t = F(float(G[7]) * 2.0 ** -8 + float(t))                 # fmaf: one rounding
+    hi = F(F(float(G[6]) + float(t)) * F(2.0 ** -32))         # one rounding, then exact
+    lo = F(0.0)
+    for d in range(5, 1, -1):
+        x = F(F(G[d]) * F(2.0 ** (-8 * (d - 2))))
+        s, e = two_sum(hi, x)
+        hi, lo = s, F(lo + e)
+    s, e = two_sum(hi, lo)
+    return Fraction(float(s)) + Fraction(float(e))
+
+
+def test_folded_chunk_product_with_group_sum():
+    """One 64-row chunk of the new rows' product as the kernel now forms it: W0_T's slices
+    by the fold, C's by error-free steps, the 26 group products exact, the groups added by
+    group_sum: within 2^-46 sigma_w sigma_c K of the exact rational product."""
+    rng = np.random.default_rng(23)
+    for trial, (scale_w, scale_c) in enumerate(((1.0, 1.0), (30.0, 1e-3), (1e-30, 5.0), (1.0, 1.0))):
+        if trial == 3:
+            wh, wl = fold_worst_cases(rng, K)
+        else:
+            wh, wl = random_df(rng, K, scale_w)
+        ch, cl = random_df(rng, K, scale_c)
+        sw, iw = pow2_scale(float(np.max(np.abs(wh))))
+        sc, ic = pow2_scale(float(np.max(np.abs(ch))))
+        A = [slices_fold(F(h * iw), F(l * iw)) for h, l in zip(wh, wl)]
+        Bm = [slices_fast(F(h * ic), F(l * ic))[0] for h, l in zip(ch, cl)]
+        G = {}
+        for d in range(2, DMAX + 1):
+            G[d] = sum(int(A[k][i - 1]) * int(Bm[k][d - i - 1]) for k in range(K) for i in range(1, SLICES + 1)
+                       if 1 <= d - i <= SLICES)
+            assert abs(G[d]) <= 2 ** 23
+        approx = group_sum(G) * Fraction(float(sw)) * Fraction(float(sc)) / 2 ** 14
+        truth = sum(exact(a, b) * exact(c, e) for a, b, c, e in zip(wh, wl, ch, cl))
+        bound = Fraction(float(sw)) * Fraction(float(sc)) * K / 2 ** 46
+        assert abs(approx - truth) <= bound, (trial, float(abs(approx - truth) / bound))
+
+
+def test_group_sum_rounding():
+    """The FP32 step of the three smallest groups costs at most 2^-33 of a unit of G_2;
+    the lazy sums and the final renormalisation add the double-float rounding, 2^-47 of
+    the value.  Cases include cancellation (G_2 = 0, small G_3)."""
+    rng = np.random.default_rng(29)
+    for t in range(3000):
+        G = {d: int(rng.integers(-2 ** 23, 2 ** 23 + 1)) for d in range(2, DMAX + 1)}
+        if t % 3 == 1:
+            G[2], G[3] = 0, int(rng.integers(-50, 51))
+        want = sum(Fraction(G[d]) * Fraction(1, 2 ** (8 * (d - 2))) for d in G)
+        assert abs(group_sum(G) - want) <= Fraction(1, 2 ** 33) + abs(want) / 2 ** 47
