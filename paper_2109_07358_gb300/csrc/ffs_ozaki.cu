@@ -15,11 +15,12 @@
 //   * the slice products a_i b_j with i + j = d <= 8 accumulate in one FP32 tensor-memory
 //     accumulator per d: every partial sum is an integer below 2^23, so the tensor-core
 //     accumulation is exact;
-//   * the epilogue adds the seven accumulators in double-float, scales by
-//     sigma_r sigma_c 2^(-14 - 8(d-2)) and subtracts from W0_T.
+//   * the epilogue adds the seven accumulators (oz_group_sum: FP32 for the three
+//     smallest, lazy error-free sums for the rest), scales by sigma_r sigma_c 2^-14 and
+//     subtracts from W0_T.
 // A real state uses the same kernels with [values | 0] rows and the real part only.
-// The dropped slice products (i + j > 8) are below 2^-46 of sigma_r sigma_c K, the order
-// of the double-float rounding of the direct update.
+// The dropped slice products (i + j > 8) and the group sums' rounding stay below 2^-46 of
+// sigma_r sigma_c K, the order of the double-float rounding of the direct update.
 //
 // Kernels per panel end: slices of A (one warp per row), slices of B (one warp per
 // column), the product (one CTA per sample and 128 old rows, looping over the trailing

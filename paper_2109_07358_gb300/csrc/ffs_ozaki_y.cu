@@ -30,7 +30,7 @@
 // issues the MMAs, warps 2-9 load W0_T from the state and write its slices straight into
 // the swizzled shared-memory operand tiles (two threads per trailing column, 32 old rows
 // each), warps 10-17 drain the accumulators (two per tensor-memory lane quarter, 16 new
-// rows each), then form Bot = S^-1 Y and write the new rows.
+// rows each); then warps 2-17 together form Bot = S^-1 Y and write the new rows.
 #include <type_traits>
 
 #include "ffs_arith.cuh"
@@ -471,14 +471,40 @@ __global__ void __launch_bounds__(kYThreads, 1)
         ((df*)&Ys[i * YCOL + cl])[rpart] = y;
       }
       for (int e = et; e < YN * YN; e += 32 * kYEpiWarps) Si[e] = ((const cdf*)t.Sinv)[(size_t)b * YN * YN + e];
-      named_sync(1, 32 * kYEpiWarps);
-      if (cval) {
-        // this thread's 8 of the column's 32 new rows: Bot = S^-1 Y in four real products
+    } else {
+      df* Ys = (df*)gbase;                     // [32 new rows][128 columns]
+      df* Si = Ys + YN * YM;                   // [32][32]
+#pragma unroll
+      for (int n = 0; n < 16; ++n) {
+        const int i = 16 * hh + n;
+        df y = df{0.f, 0.f};
+        if (cval) {
+          const int xi = a.x[b * a.ldx + k0 + i];
+          y = df_sub(((const df*)a.Ust)[(int64_t)xi * a.N + mc], lz_get(yacc[n]));
+        }
+        Ys[i * YM + cl] = y;
+      }
+      for (int e = et; e < YN * YN; e += 32 * kYEpiWarps) Si[e] = ((const df*)t.Sinv)[(size_t)b * YN * YN + e];
+    }
+    (void)dead;
+  }
+  if (warp >= 2) {
+    // Bot = S^-1 Y and the new rows, on the producer and epilogue warps together (512
+    // threads; the producers are done with their chunks).  Every one of them reaches
+    // this barrier exactly once, also after a failed wait.
+    named_sync(1, 32 * (kYProdWarps + kYEpiWarps));
+    const int u = threadIdx.x - 64;  // 0 .. 511
+    if constexpr (CX) {
+      const cdf* Ys = (const cdf*)gbase;  // [32 new rows][64 columns]
+      const cdf* Si = Ys + YN * YCOL;     // [32][32]
+      const int cl = u & (YCOL - 1), rg = u >> 6;  // column, rows 4 rg .. 4 rg + 3
+      const int64_t c = c0 + cl;
+      if (c < Nc) {
         cdf* Wn = (cdf*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
         // two rows at a time (four independent accumulation chains)
 #pragma unroll 1
-        for (int n0 = 0; n0 < 8; n0 += 2) {
-          const int i0 = 16 * hh + 8 * rpart + n0;
+        for (int n0 = 0; n0 < 4; n0 += 2) {
+          const int i0 = 4 * rg + n0;
           lzf re[2], im[2];
 #pragma unroll
           for (int r = 0; r < 2; ++r) re[r] = im[r] = lzf{0.f, 0.f};
@@ -499,26 +525,16 @@ __global__ void __launch_bounds__(kYThreads, 1)
         }
       }
     } else {
-      df* Ys = (df*)gbase;                     // [32 new rows][128 columns]
-      df* Si = Ys + YN * YM;                   // [32][32]
-#pragma unroll
-      for (int n = 0; n < 16; ++n) {
-        const int i = 16 * hh + n;
-        df y = df{0.f, 0.f};
-        if (cval) {
-          const int xi = a.x[b * a.ldx + k0 + i];
-          y = df_sub(((const df*)a.Ust)[(int64_t)xi * a.N + mc], lz_get(yacc[n]));
-        }
-        Ys[i * YM + cl] = y;
-      }
-      for (int e = et; e < YN * YN; e += 32 * kYEpiWarps) Si[e] = ((const df*)t.Sinv)[(size_t)b * YN * YN + e];
-      named_sync(1, 32 * kYEpiWarps);
-      if (cval) {
+      const df* Ys = (const df*)gbase;  // [32 new rows][128 columns]
+      const df* Si = Ys + YN * YM;      // [32][32]
+      const int cl = u & (YM - 1), rg = u >> 7;  // column, rows 8 rg .. 8 rg + 7
+      const int64_t c = c0 + cl;
+      if (c < Nc) {
         df* Wn = (df*)t.W + (size_t)b * state_stride(Nc) + (size_t)slab_offset(c >> 5) + (c & 31);
         // four rows at a time: four independent accumulation chains share each Y entry
 #pragma unroll 1
-        for (int n0 = 0; n0 < 16; n0 += 4) {
-          const int i0 = 16 * hh + n0;
+        for (int n0 = 0; n0 < 8; n0 += 4) {
+          const int i0 = 8 * rg + n0;
           lzf acc[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) acc[r] = lzf{0.f, 0.f};
@@ -533,7 +549,6 @@ __global__ void __launch_bounds__(kYThreads, 1)
         }
       }
     }
-    (void)dead;
   }
   tc_fence_before();
   __syncthreads();
