@@ -372,96 +372,93 @@ __device__ __forceinline__ void step_update(const StepArgs& a, const BlockedArgs
   const int32_t* mrow = a.m + b * N;
   const A* urow = (const A*)a.Ust + (int64_t)x * N;  // U in the state type
   const bool live = lane < k1 - k0;                  // the column exists
-  const bool need = live && lane >= i - 1;           // columns k-1 .. k1-1 are read
   const bool gem = live && lane >= i;                // columns k .. k1-1 are reduced
   const bool pend = i >= 1;                          // an update of step k-1 is pending
   const bool keep = i == 0 && k0 > 0;                // first step of a panel: save W0_P
-  const A nprev = (pend && gem) ? Wp[(k - 1) * 32 + lane] : T::zero();  // new row of step k-1
-  const int src = pend ? i - 1 : 0;                  // lane of column k-1
 
   // one pass over the rows: pending update, write-back, reduction
-  // r'[c] = u[c] - sum_{j<k} u[j] W[j][c] (rows in groups of G whose loads are issued
-  // together; two accumulation chains)
-  constexpr int G = kStepRowGroup;
+  // r'[c] = u[c] - sum_{j<k} u[j] W[j][c].  Only the columns from k-1 on are read (all of
+  // them at a panel's first step), so a warp takes P = 32 / S rows at a time, S the
+  // smallest power of two >= the number of those columns: lane = (row slot rr, column
+  // cs + cc).  Late in a panel, with few columns left, one instruction then covers
+  // several rows.
+  const int cs = i >= 1 ? i - 1 : 0;                 // first column read (k-1 when pending)
+  const int ncol = (int)(k1 - k0) - cs;              // columns cs .. k1-k0-1
+  const int lgS = ncol > 16 ? 5 : ncol > 8 ? 4 : ncol > 4 ? 3 : ncol > 2 ? 2 : ncol > 1 ? 1 : 0;
+  const int S = 1 << lgS, P = 32 >> lgS;
+  const int rr = lane >> lgS, cc = lane & (S - 1);
+  const int lc = cs + cc;                            // this lane's column
+  const bool live_c = cc < ncol;
+  const bool gem_c = live_c && lc >= i;
+  const A nprev = (pend && gem_c) ? Wp[(k - 1) * 32 + lc] : T::zero();  // new row of step k-1
+  const int src = rr << lgS;                         // lane of column k-1 in this row slot
+
+  // rows in groups of G passes whose loads are issued together (one group of lookahead for
+  // 4- and 8-byte entries: the next group's loads go out before this group's stores, which
+  // the compiler cannot do on its own; 16-byte entries take one pass per group, loaded in
+  // turn, which keeps them at 64 registers); two accumulation chains
+  constexpr bool kAhead = sizeof(A) <= 8;
+  constexpr int G = kAhead ? kStepRowGroup : 1;      // 16-byte entries: one pass per group
+  const int64_t grp = (int64_t)P * G;                // rows per group
   A acc = T::zero(), acc2 = T::zero();
-  // rows stream from DRAM: keep the next 32-row groups on their way into L2, two groups
+  // rows stream from DRAM: keep the next 32-row blocks on their way into L2, two blocks
   // ahead of the loads; lane l prefetches row j + l from the first column read (rounded
   // down to 16 bytes) to the end of the row, so late in a panel, when few columns are
   // live, the prefetch does not drag the dead part of each row out of DRAM
   constexpr int kColAlign = sizeof(A) >= 16 ? 1 : (int)(16 / sizeof(A));
-  const int cpf = (i >= 1 ? i - 1 : 0) & ~(kColAlign - 1);
+  const int cpf = cs & ~(kColAlign - 1);
   const uint32_t pf_bytes = (uint32_t)((32 - cpf) * sizeof(A));
   auto prefetch_rows = [&](int64_t j) {
     if (j + lane < k) sm100::prefetch_l2_bulk(Wp + (j + lane) * 32 + cpf, pf_bytes);
   };
-  prefetch_rows(0);
-  prefetch_rows(32);
-  for (int64_t j0 = 0; j0 < k; j0 += 32) {
-    prefetch_rows(j0 + 64);
-    const int64_t jl = j0 + lane;
-    const A uj = (jl < k) ? urow[mrow[jl]] : T::zero();
-    const int jn = (int)min((int64_t)32, k - j0);
-    int jj = 0;
-    // one group of lookahead for 4- and 8-byte entries: the next group's loads are issued
-    // before this group's stores (the compiler cannot move them across the stores on its
-    // own); 16-byte (complex double-float / FP64) entries load each group in turn, which
-    // keeps them at 64 registers without spilling
-    constexpr bool kAhead = sizeof(A) <= 8;
-    A wv[G];
+  auto ld_w = [&](int64_t j) { return (j < k && live_c) ? Wp[j * 32 + lc] : T::zero(); };
+  auto ld_u = [&](int64_t j) { return j < k ? urow[mrow[j]] : T::zero(); };
+  int64_t pf = 0;
+  A wv[G];
+  if constexpr (kAhead) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) wv[g] = ld_w((int64_t)g * P + rr);
+  }
+  for (int64_t jb = 0; jb < k; jb += grp) {
+    for (; pf < jb + grp + 64 && pf < k; pf += 32) prefetch_rows(pf);
+    A wn[G], uv[G];
     if constexpr (kAhead) {
 #pragma unroll
-      for (int q = 0; q < G; ++q) wv[q] = (need && G <= jn) ? Wp[(j0 + q) * 32 + lane] : T::zero();
+      for (int g = 0; g < G; ++g) wn[g] = ld_w(jb + grp + (int64_t)g * P + rr);
+    } else {
+#pragma unroll
+      for (int g = 0; g < G; ++g) wv[g] = ld_w(jb + (int64_t)g * P + rr);
     }
-    for (; jj + G <= jn; jj += G) {
-      A wnx[G];
-      const bool more = jj + 2 * G <= jn;
-      if constexpr (kAhead) {
 #pragma unroll
-        for (int q = 0; q < G; ++q) wnx[q] = (need && more) ? Wp[(j0 + jj + G + q) * 32 + lane] : T::zero();
-      } else {
+    for (int g = 0; g < G; ++g) uv[g] = ld_u(jb + (int64_t)g * P + rr);  // cached: U's row x
 #pragma unroll
-        for (int q = 0; q < G; ++q) wv[q] = need ? Wp[(j0 + jj + q) * 32 + lane] : T::zero();
-      }
-      if (keep && live) {
-#pragma unroll
-        for (int q = 0; q < G; ++q) W0P[(j0 + jj + q) * NB + lane] = wv[q];
-      }
+    for (int g = 0; g < G; ++g) {
+      const int64_t j = jb + (int64_t)g * P + rr;
+      if (keep && live_c && j < k) W0P[j * NB + lc] = wv[g];
       if (pend) {
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-          const A wk = shfl_idx_any(wv[q], src);
-          if (gem && j0 + jj + q < k - 1) {
-            wv[q] = T::fms(wv[q], wk, nprev);
-            Wp[(j0 + jj + q) * 32 + lane] = wv[q];
-          }
+        const A wk = shfl_idx_any(wv[g], src);
+        if (gem_c && j < k - 1) {
+          wv[g] = T::fms(wv[g], wk, nprev);
+          Wp[j * 32 + lc] = wv[g];
         }
       }
-#pragma unroll
-      for (int q = 0; q < G; q += 2) {
-        acc = T::fms(acc, shfl_idx_any(uj, jj + q), gem ? wv[q] : T::zero());
-        acc2 = T::fms(acc2, shfl_idx_any(uj, jj + q + 1), gem ? wv[q + 1] : T::zero());
-      }
-      if constexpr (kAhead) {
-#pragma unroll
-        for (int q = 0; q < G; ++q) wv[q] = wnx[q];
-      }
     }
-    for (; jj < jn; ++jj) {
-      const int64_t j = j0 + jj;
-      A w = need ? Wp[j * 32 + lane] : T::zero();
-      if (keep && live) W0P[j * NB + lane] = w;
-      if (pend) {
-        const A wk = shfl_idx_any(w, src);
-        if (gem && j < k - 1) {
-          w = T::fms(w, wk, nprev);
-          Wp[j * 32 + lane] = w;
-        }
-      }
-      const A u = shfl_idx_any(uj, jj);
-      if (gem) acc = T::fms(acc, u, w);
+#pragma unroll
+    for (int g = 0; g < G; g += 2) {
+      acc = T::fms(acc, uv[g], gem_c ? wv[g] : T::zero());
+      if (g + 1 < G) acc2 = T::fms(acc2, uv[g + 1], gem_c ? wv[g + 1] : T::zero());
+    }
+    if constexpr (kAhead) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) wv[g] = wn[g];
     }
   }
   acc = T::add(acc, acc2);
+  // the row slots' partial sums of each column (the same total in every slot), then
+  // column l's total into lane l
+  for (int o = S; o < 32; o <<= 1) acc = T::add(acc, shfl_xor_any(acc, o));
+  const int from = lane - cs;
+  acc = shfl_idx_any(acc, (from >= 0 && from < S) ? from : 0);
   const A rc = gem ? T::add(urow[mrow[k0 + lane]], acc) : T::zero();
   const A s = shfl_idx_any(rc, i);  // pivot: the Schur residual of x_k
   if (lane == 0) {
