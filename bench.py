@@ -623,6 +623,20 @@ def run_timed(S, B, steps, warmup, rank, world, stream, x, local, flush_needed, 
     return step, flush, evs
 
 
+def kernel_launches(res_n, tail_n, panel_n, pans_n, ptc_n, perm_n, N, nb=32):
+    """Kernel launches behind the profiler's phase counts.  Each phase count is one timed
+    region; with the tensor-core trailing update a panel end's regions hold several
+    kernels: the new rows are C's slices + ozy_kernel (ozy alone when no old rows exist,
+    k0 = 0), the old rows are two slice kernels + the product + the next operand (the
+    operand alone at k0 = 0)."""
+    n = res_n + tail_n + panel_n + pans_n + ptc_n + perm_n
+    if ptc_n:
+        ends = sum(1 for k0 in range(0, N, nb) if min(k0 + nb, N) < N)  # panel ends per wave-step
+        first = panel_n / ends if ends else 0                          # those with k0 = 0
+        n += (panel_n - first) + 3 * (ptc_n - first)
+    return int(round(n))
+
+
 def phase_report(prof, L, N, B, K, cplx, chosen, state, peaks, trailing_tc):
     """Per-phase times and rates, the residual (GEMM) roofline against the tensor-core
     peak of its precision, and the state update's dominant kernel against its peak."""
@@ -708,7 +722,7 @@ def phase_report(prof, L, N, B, K, cplx, chosen, state, peaks, trailing_tc):
                                      "tail_panel_tc": "per sample-panel: W0_T read and Top written, W0_P read"}[dom]
                                     + f" ({e}-byte entries)",
                      "share_of_step": cands[dom] / total_ms}
-        launches = int(res_n + tail_n + panel_n + pans_n + ptc_n + perm_n) // K
+        launches = kernel_launches(res_n, tail_n, panel_n, pans_n, ptc_n, perm_n, N) // K
         return phases, roof, roof_tail, launches
     # the CUDA-core new-row kernel against the peak of its own arithmetic
     if state == "df64":
@@ -727,7 +741,7 @@ def phase_report(prof, L, N, B, K, cplx, chosen, state, peaks, trailing_tc):
                  "achieved": tail_ach, "peak": st_peak, "unit": "TFLOP/s",
                  "frac": tail_ach / st_peak if tail_ach else None,
                  "traffic": None, "peak_source": st_src, "share_of_step": panel_ms / total_ms}
-    launches = int(res_n + tail_n + panel_n + pans_n + ptc_n + perm_n) // K
+    launches = kernel_launches(res_n, tail_n, panel_n, pans_n, ptc_n, perm_n, N) // K
     return phases, roof, roof_tail, launches
 
 def section(out, name, fn):
