@@ -84,3 +84,31 @@ def test_oracle_plan_large_workload_uses_all_cores_in_one_process():
     small = w.chain_L64_N8()
     n, threads = bench.oracle_plan(small, 100, target_s=0.2)
     assert threads == 1 and n >= 2
+
+
+def test_kernel_launch_count_matches_the_launch_structure():
+    # Anderson chain N = 2048, one wave, K = 3 steps: per step 2048 residual and per-step
+    # launches, one permutation kernel, and at the 63 panel ends panel_s, the new-row
+    # kernel (+ C's slices when k0 > 0) and the old-row pass (two slice kernels and the
+    # product when k0 > 0, the operand kernel always): 4534, the count of the ncu list
+    K, ends = 3, 63
+    n = bench.kernel_launches(2048 * K, 2048 * K, ends * K, ends * K, ends * K, K, 2048)
+    assert n // K == 2048 + 2048 + 1 + ends + (ends + ends - 1) + (ends + 3 * (ends - 1))
+    assert n // K == 4534
+    # two waves double every count, including the panel ends without old rows
+    n2 = bench.kernel_launches(2 * 2048 * K, 2 * 2048 * K, 2 * ends * K, 2 * ends * K, 2 * ends * K, 2 * K, 2048)
+    assert n2 == 2 * n
+    # without the tensor-core trailing update each region is one kernel
+    assert bench.kernel_launches(10, 10, 2, 2, 0, 1, 2048) == 25
+
+
+def test_blocked_bytes_model():
+    L, N, e = 4096, 96, 8
+    full = bench.blocked_bytes_per_sample(L, N, e)
+    gs = bench.blocked_bytes_per_sample(L, N, e, gsum=32)
+    # the draw reads L / 32 sums and one group of 32 weights instead of all L weights
+    assert full["step"] - gs["step"] == N * 4 * (L - (L // 32 + 32))
+    assert full["new"] == gs["new"] and full["top"] == gs["top"]
+    # panel ends: k0 = 0 (T = 64) and k0 = 32 (T = 32); k0 = 64 ends the chain
+    assert full["new"] == e * ((0 * 64 + 2 * 32 * 64) + (32 * 32 + 2 * 32 * 32))
+    assert full["top"] == e * ((2 * 0 * 64 + 0) + (2 * 32 * 32 + 32 * 32))
