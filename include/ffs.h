@@ -92,13 +92,14 @@ typedef enum {
  *                     be a multiple of 128; not available to ffs_sample_batched, the serving
  *                     engine, ffs_sample_lensemble or ffs_sample_metropolis.
  * Trailing update:
- *   FFS_TRAILING_TC  opt-in: the once-per-panel update of the old rows' remaining columns
- *                    runs on the tensor cores through an error-free split of the
- *                    double-float operands into BF16 slices (products exact in FP32
- *                    accumulation, double-float epilogue).  FFS_STATE_DF64, the blocked
- *                    state and a tensor-core residual only (else FFS_E_UNSUPPORTED at
- *                    creation).  It pays for complex U; for real U half of each slice
- *                    row is zero padding and the direct update is as fast or faster.
+ *   FFS_TRAILING_TC  opt-in: the once-per-panel trailing update (the new rows
+ *                    Y = U[x_new, m_T] - C W0_T with Bot = S^-1 Y, and the old rows
+ *                    Top = W0_T - W0_P Bot) runs on the tensor cores through a split of the
+ *                    double-float operands into six BF16 slices each (slice products exact
+ *                    in FP32 accumulation, each block's product within 2^-46 of its scales
+ *                    times K).  FFS_STATE_DF64, the blocked state and a tensor-core
+ *                    residual only (else FFS_E_UNSUPPORTED at creation).  Real and complex
+ *                    U; the benchmark's chosen form.
  * Checks:
  *   FFS_NO_ORTHO_CHECK  skip the U^dagger U = 1 check in ffs_create_ex
  */

@@ -146,8 +146,9 @@ struct OzArgs {
   int64_t KP, TP;
 };
 
-// C's slices for the tensor-core new-row update (real state): [b][chunk][slice][32][64]
-// BF16 and the row scales [b][chunk][32]; n_chunks = chunks of 64 old rows per sample.
+// C's slices for the tensor-core new-row update: [b][chunk][slice][32][64] BF16 and the
+// row scales [b][chunk][32]; n_chunks = chunks of 64 K elements per sample (64 old rows
+// of a real state, 32 of a complex one as interleaved real and imaginary parts).
 struct OzYArgs {
   __nv_bfloat16* C;
   float* Cs;
